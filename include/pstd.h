@@ -1,0 +1,155 @@
+/*
+ * pstd.h -- C ABI of the GB300 DTT-based PSTD library.
+ *
+ * The library time-steps the linear acoustic equations (Eq. wave_eq)
+ *     du/dt = -(1/rho0) dp/dx,   dp/dt = -rho0 c0^2 du/dx
+ * in a 1-, 2- or 3-D box whose walls are each Neumann (sound-hard) or
+ * Dirichlet (sound-soft), with the sine/cosine pseudospectral scheme of
+ * Wise, Jaros, Cox & Treeby (Section 4, Eq. dtt_pstd_solution and its n-D
+ * form in Section 4.3):
+ *     u_i^{n+1/2} = u_i^{n-1/2} - (dt/rho0)       T_{i,2}^{-1}{ a_{i,1} T_{i,1}{ p^n } }
+ *     p^{n+1}     = p^n - dt rho0 c0^2 sum_i      T_{i,1}^{-1}{ a_{i,2} T_{i,2}{ u_i^{n+1/2} } }
+ * with the transform pair (T1, T2) and k-space coefficients (a1, a2) of each
+ * axis chosen from its wall pair by Table 2.
+ *
+ * Grid and memory layout (all fields FP32, C order, axis 0 slowest):
+ *   - N_i cells of width dx_i per axis; walls at x = 0 and x = N_i dx_i.
+ *   - Pressure p lives on the nodes x_j = j dx.  Nodes on a Dirichlet wall
+ *     (where p = 0 identically) are not stored, so along axis i p has
+ *     N_i+1 (NN), N_i (ND, DN) or N_i-1 (DD) entries, starting at node 0 for
+ *     a Neumann left wall and at node 1 for a Dirichlet one.
+ *   - Velocity u_i lives on the N_i half-nodes (m + 1/2) dx_i along axis i and
+ *     on the stored pressure nodes along every other axis.
+ *   pstd_field_shape() returns these shapes.
+ *
+ * Ownership: the caller allocates and owns every field buffer (device
+ * memory, contiguous, FP32, 256-byte aligned as cudaMalloc / torch return it).
+ * The plan owns its tables and its scratch accumulator and frees them in
+ * pstd_free().
+ *
+ * Streams and errors: every call that touches device memory enqueues work on
+ * the plan's stream and returns without synchronising.  Return value 0 is
+ * success; negative values are the PSTD_E* codes below.  No C++ exception
+ * crosses this interface.  A CUDA launch error is reported by the call that
+ * launched; errors raised while the device runs surface at pstd_sync().
+ * A plan is not thread-safe: do not call into one plan from two host
+ * threads at once.
+ */
+#ifndef PSTD_H
+#define PSTD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Wall type.  Table 2: Neumann <-> whole-sample symmetric pressure,
+ * Dirichlet <-> whole-sample antisymmetric pressure. */
+typedef enum { PSTD_NEUMANN = 0, PSTD_DIRICHLET = 1 } pstd_bc;
+
+/* How pstd_init_velocity derives u^{-1/2} from the given u(0).
+ * PSTD_U_HALFSTEP: u^{-1/2} = u0 + (dt / (2 rho0)) D_p p^0, so that the
+ *   time-centred velocity equals u0 at t = 0 (the staggered-grid reading of
+ *   "initial particle velocity set to zero" in Section 4.2).
+ * PSTD_U_AS_GIVEN: u^{-1/2} = u0. */
+typedef enum { PSTD_U_HALFSTEP = 0, PSTD_U_AS_GIVEN = 1 } pstd_uinit;
+
+enum {
+    PSTD_OK = 0,
+    PSTD_EINVAL = -1,       /* bad descriptor, pointer, axis or field index */
+    PSTD_EUNSTABLE = -2,    /* c0 dt |k|_max / 2 > 1: beyond the leapfrog limit */
+    PSTD_ENOMEM = -3,       /* device or host allocation failed */
+    PSTD_ECUDA = -4,        /* a CUDA runtime call failed (see pstd_last_cuda_error) */
+    PSTD_ETIMEOUT = -5,     /* a bounded device-side wait gave up */
+    PSTD_EUNSUPPORTED = -6  /* size with no transform schedule (see pstd_plan) */
+};
+
+/* Problem statement (Section 4.1 / 4.3; the time step dt = CFL dx / c0 of
+ * Section 4.2 is given explicitly, see pstd_dt_from_cfl). */
+typedef struct {
+    int ndim;              /* 1, 2 or 3 */
+    int64_t ncells[3];     /* N_i >= 1 cells per axis (M_i = 2 N_i) */
+    double dx[3];          /* grid spacing per axis [m] */
+    int bc[3][2];          /* pstd_bc of the [axis][left, right] walls */
+    double c0;             /* sound speed [m/s] */
+    double rho0;           /* density [kg/m^3] */
+    double dt;             /* time step [s] */
+    int uinit;             /* pstd_uinit */
+} pstd_desc;
+
+typedef struct pstd_plan_s pstd_plan_t;
+
+/* Validate a descriptor and build a plan on the current CUDA device.
+ * Builds the FP64 tables (twiddles, wavenumbers, folded k-space
+ * coefficients -(dt/rho0) i k e^{+ik dx/2} / M and -(dt rho0 c0^2) i k
+ * e^{-ik dx/2} / M of the symmetric-periodic extension of each axis, Table 1)
+ * and rounds them once to FP32; allocates them and one scratch accumulator of
+ * the pressure shape (ndim >= 2) on the device.  Axes whose 2 N_i factors
+ * into 2, 3 and 5 use shared-memory FFT kernels; other axes with N_i <= 256
+ * use a dense operator matrix; larger other axes return PSTD_EUNSUPPORTED.
+ * `stream` is a cudaStream_t (NULL = legacy default stream).
+ * Errors: PSTD_EINVAL (ndim, N_i, dx, c0, rho0, dt, bc or uinit out of
+ * range; N_i = 1 with DD walls has no pressure node), PSTD_EUNSTABLE,
+ * PSTD_EUNSUPPORTED, PSTD_ENOMEM, PSTD_ECUDA.  *out is NULL on error. */
+int pstd_plan(const pstd_desc* desc, void* stream, pstd_plan_t** out);
+
+/* Shape of field 0 (p) or field i+1 (u_i) as three extents (unused axes 1).
+ * Errors: PSTD_EINVAL. */
+int pstd_field_shape(const pstd_plan_t* plan, int field, int64_t shape[3]);
+
+/* Elements of field `field` (0 = p, i+1 = u_i); 0 on a bad index. */
+int64_t pstd_field_numel(const pstd_plan_t* plan, int field);
+
+/* Staggered spectral derivative along `axis` of one field, without time
+ * stepping (Section 3.4, Tables A3 / A6):
+ *   dir 0: out = T2^{-1}{ a1 T1{ in } }  (in: pressure-shaped, out: u_axis-shaped)
+ *   dir 1: out = T1^{-1}{ a2 T2{ in } }  (in: u_axis-shaped,   out: pressure-shaped)
+ * `in` and `out` are device pointers that must not overlap.
+ * Errors: PSTD_EINVAL, PSTD_ECUDA. */
+int pstd_grad(pstd_plan_t* plan, int axis, int dir, const float* in, float* out);
+
+/* Derive u^{-1/2} in place from p^0 and the velocities already in u[0..ndim-1]
+ * according to desc->uinit (PSTD_U_AS_GIVEN leaves u untouched).
+ * Errors: PSTD_EINVAL, PSTD_ECUDA. */
+int pstd_init_velocity(pstd_plan_t* plan, const float* p0, float* const* u);
+
+/* One leapfrog step in place: (p^n, u^{n-1/2}) -> (p^{n+1}, u^{n+1/2}).
+ * `u` is a host array of ndim device pointers.  Errors: PSTD_EINVAL, PSTD_ECUDA. */
+int pstd_step(pstd_plan_t* plan, float* p, float* const* u);
+
+/* `nsteps` >= 0 leapfrog steps in place.  The plan records one block of
+ * steps in a CUDA graph per (p, u) pointer set on first use and replays it;
+ * a tail shorter than the block is launched directly.
+ * Errors: PSTD_EINVAL, PSTD_ECUDA. */
+int pstd_run(pstd_plan_t* plan, float* p, float* const* u, int64_t nsteps);
+
+/* Synchronise the plan's stream; reports device-side errors.
+ * Errors: PSTD_ECUDA. */
+int pstd_sync(pstd_plan_t* plan);
+
+/* Release the plan (synchronises its stream first).  NULL is a no-op. */
+int pstd_free(pstd_plan_t* plan);
+
+/* Static description of an error code. */
+const char* pstd_strerror(int code);
+
+/* Text of the last CUDA error seen by any call on this thread ("" if none). */
+const char* pstd_last_cuda_error(void);
+
+/* dt = CFL dx / c0 (Section 4.2). */
+double pstd_dt_from_cfl(double cfl, double dx, double c0);
+
+/* Number of kernels the last pstd_step / pstd_run / pstd_grad /
+ * pstd_init_velocity call on this plan launched (graph replays count their
+ * kernel nodes). */
+int64_t pstd_last_launch_count(const pstd_plan_t* plan);
+
+/* Library version string. */
+const char* pstd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSTD_H */

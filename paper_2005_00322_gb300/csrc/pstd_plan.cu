@@ -1,0 +1,550 @@
+// pstd_plan.cu -- host side of the C ABI declared in include/pstd.h.
+//
+// A plan holds, per axis, the FP64-built / FP32-stored tables of the two
+// staggered derivatives (Section 3.4 with Table 1's wavenumbers and Table 2's
+// transform choice, evaluated as the Fourier multiplier on the symmetric-
+// periodic extension), the launch geometry of the axis pass, and one scratch
+// accumulator of the pressure shape.  A leapfrog step (Eq. dtt_pstd_solution,
+// n-D form of Section 4.3) launches one fused pass per axis, last axis first:
+//     axis d-1:     u_{d-1} += f_P(p);  S = p + f_U(u_{d-1})
+//     axis 1..d-2:  u_a     += f_P(p);  S = S + f_U(u_a)
+//     axis 0:       u_0     += f_P(p);  p = S + f_U(u_0)
+// (1-D: u += f_P(p); p = p + f_U(u)).  Every pass reads p^n, which no pass of
+// the same step overwrites before the last one, and the last pass writes each
+// p line only after the CTA that owns it has read it.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pstd.h"
+#include "pstd_cta.cuh"
+
+namespace pstd {
+// Launchers and attribute setup, defined with the kernels (pstd_kernels.cu).
+cudaError_t launch_k_step(unsigned grid, size_t smem, cudaStream_t st, const StepArgs& a);
+cudaError_t launch_k_grad(unsigned grid, size_t smem, cudaStream_t st, const GradArgs& a);
+cudaError_t set_max_smem(int bytes);
+}  // namespace pstd
+
+using pstd::FftPlan;
+using pstd::GradArgs;
+using pstd::LineOp;
+using pstd::StepArgs;
+
+namespace {
+
+thread_local std::string g_cuda_err;
+
+constexpr int kDenseMaxN = 256;
+constexpr int kGraphSteps = 32;
+constexpr int kGraphCache = 4;
+constexpr size_t kSmemBudget = 100 * 1024;
+
+enum { OP_GRAD_P = 0, OP_GRAD_U = 1, OP_STEP_P = 2, OP_STEP_U = 3, OP_INIT_P = 4, OP_COUNT = 5 };
+
+struct Axis {
+    int N = 0, L = 0, group2 = 0, kind = 0;
+    int lp = 0, lo = 0;               // stored pressure length, first stored node
+    double dx = 0;
+    int bcl = 0, bcr = 0;
+    FftPlan fft{};
+    float2* d_tw = nullptr;
+    float2* d_shift = nullptr;
+    float2* d_f[OP_COUNT] = {};
+    float* d_dense[OP_COUNT] = {};
+    LineOp op[OP_COUNT];
+    int64_t nlines = 0, inner = 1;
+    int G = 2, rs = 1;
+    size_t smem = 0;
+};
+
+struct GraphEntry {
+    float* p = nullptr;
+    float* u[3] = {nullptr, nullptr, nullptr};
+    cudaGraphExec_t exec = nullptr;
+    int steps = 0;
+    int64_t launches = 0;
+    uint64_t stamp = 0;
+};
+
+int cuda_fail(cudaError_t e, const char* what) {
+    g_cuda_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return PSTD_ECUDA;
+}
+
+#define CK(call)                                         \
+    do {                                                 \
+        cudaError_t _e = (call);                         \
+        if (_e != cudaSuccess) return cuda_fail(_e, #call); \
+    } while (0)
+
+// Radix schedule of L over {8, 4, 2, 3, 5}; false if L has another factor.
+bool radix_schedule(int L, FftPlan& P) {
+    int r = L;
+    P.L = L;
+    P.npass = 0;
+    int twos = 0;
+    while (r % 2 == 0) { r /= 2; ++twos; }
+    int threes = 0;
+    while (r % 3 == 0) { r /= 3; ++threes; }
+    int fives = 0;
+    while (r % 5 == 0) { r /= 5; ++fives; }
+    if (r != 1 || L < 2) return false;
+    auto push = [&](int R) {
+        if (P.npass >= pstd::kMaxPasses) return false;
+        P.radix[P.npass++] = R;
+        return true;
+    };
+    while (twos >= 3) { if (!push(8)) return false; twos -= 3; }
+    if (twos == 2) { if (!push(4)) return false; }
+    if (twos == 1) { if (!push(2)) return false; }
+    for (int i = 0; i < threes; ++i) if (!push(3)) return false;
+    for (int i = 0; i < fives; ++i) if (!push(5)) return false;
+    return true;
+}
+
+}  // namespace
+
+struct pstd_plan_s {
+    pstd_desc desc{};
+    cudaStream_t stream = nullptr;
+    int ndim = 0;
+    int64_t shape[4][3] = {};
+    Axis ax[3];
+    float* d_S = nullptr;
+    int64_t last_launches = 0;
+    GraphEntry graphs[kGraphCache];
+    uint64_t stamp = 0;
+};
+
+namespace {
+
+// Folded coefficient f_n of the extension's Fourier multiplier (Table 1
+// wavenumbers; shift +dx/2 for p -> u, -dx/2 for u -> p), including 1/M.
+std::complex<double> coeff(const Axis& a, int n, int dir, double scale) {
+    const int N = a.N, L = a.L;
+    double kap;
+    bool nyquist = false;
+    if (!a.group2) {
+        const int nn = n <= N ? n : n - L;
+        kap = 2.0 * M_PI * nn / (L * a.dx);
+        nyquist = (n == N);
+    } else {
+        const int nn = n < N ? n : n - L;
+        kap = M_PI * (2.0 * nn + 1.0) / (L * a.dx);
+    }
+    const double s = dir == 0 ? 0.5 * a.dx : -0.5 * a.dx;
+    // i kap exp(i kap s) = (-kap sin(kap s), kap cos(kap s))
+    double re = -kap * std::sin(kap * s);
+    double im = nyquist ? 0.0 : kap * std::cos(kap * s);
+    return std::complex<double>(re, im) * (scale / L);
+}
+
+template <class T>
+int upload(const std::vector<T>& h, T** d) {
+    CK(cudaMalloc((void**)d, h.size() * sizeof(T)));
+    CK(cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return PSTD_OK;
+}
+
+// Dense operator (rows: stored outputs, cols: stored inputs) of the same
+// multiplier, FP64, for axes with no FFT schedule.
+std::vector<float> dense_operator(const Axis& a, int dir, double scale) {
+    const int N = a.N, L = a.L;
+    std::vector<std::complex<double>> K(L);
+    for (int d = 0; d < L; ++d) {
+        std::complex<double> acc = 0;
+        for (int n = 0; n < L; ++n) {
+            const double ang = 2.0 * M_PI * (double)((int64_t)d * n % L) / L;
+            acc += coeff(a, n, dir, scale) * std::complex<double>(std::cos(ang), std::sin(ang));
+        }
+        K[d] = acc;
+    }
+    const int nin = dir == 0 ? a.lp : N;
+    const int nout = dir == 0 ? N : a.lp;
+    const double sR = dir == 0 ? (a.bcr == PSTD_NEUMANN ? 1.0 : -1.0)
+                               : (a.bcr == PSTD_NEUMANN ? -1.0 : 1.0);
+    std::vector<float> D((size_t)nout * nin);
+    for (int i = 0; i < nout; ++i) {
+        const int pos = dir == 0 ? i : i + a.lo;
+        for (int j = 0; j < nin; ++j) {
+            int src[2];
+            double sg[2];
+            int nimg = 0;
+            if (dir == 0) {
+                const int q = j + a.lo;
+                src[nimg] = q; sg[nimg++] = 1.0;
+                if (q > 0 && q < N) { src[nimg] = 2 * N - q; sg[nimg++] = sR; }
+            } else {
+                src[nimg] = j; sg[nimg++] = 1.0;
+                src[nimg] = 2 * N - 1 - j; sg[nimg++] = sR;
+            }
+            double v = 0;
+            for (int m = 0; m < nimg; ++m) {
+                const int delta = pos - src[m];
+                std::complex<double> k = K[((delta % L) + L) % L];
+                if (a.group2) {
+                    const double ang = M_PI * delta / L;
+                    k *= std::complex<double>(std::cos(ang), std::sin(ang));
+                }
+                v += sg[m] * k.real();
+            }
+            D[(size_t)i * nin + j] = (float)v;
+        }
+    }
+    return D;
+}
+
+int build_axis(pstd_plan_s* P, int i) {
+    Axis& a = P->ax[i];
+    const pstd_desc& d = P->desc;
+    a.N = (int)d.ncells[i];
+    a.L = 2 * a.N;
+    a.dx = d.dx[i];
+    a.bcl = d.bc[i][0];
+    a.bcr = d.bc[i][1];
+    a.group2 = a.bcl != a.bcr;
+    a.lo = a.bcl == PSTD_DIRICHLET ? 1 : 0;
+    const int hi = a.bcr == PSTD_DIRICHLET ? a.N - 1 : a.N;
+    a.lp = hi - a.lo + 1;
+    const bool fft_ok = radix_schedule(a.L, a.fft);
+    if (!fft_ok && a.N > kDenseMaxN) return PSTD_EUNSUPPORTED;
+    a.kind = fft_ok ? 0 : 1;
+
+    // twiddles and group-II shifts, FP64 -> FP32 once
+    std::vector<float2> tw(a.L), sh(a.L);
+    for (int m = 0; m < a.L; ++m) {
+        const double ang = 2.0 * M_PI * m / a.L;
+        tw[m] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+        const double ang2 = M_PI * m / a.L;
+        sh[m] = make_float2((float)std::cos(ang2), (float)-std::sin(ang2));
+    }
+    int rc;
+    if ((rc = upload(tw, &a.d_tw)) != PSTD_OK) return rc;
+    if ((rc = upload(sh, &a.d_shift)) != PSTD_OK) return rc;
+    a.fft.tw = a.d_tw;
+
+    const double scales[OP_COUNT] = {1.0, 1.0, -d.dt / d.rho0, -d.dt * d.rho0 * d.c0 * d.c0,
+                                     d.dt / (2.0 * d.rho0)};
+    const int dirs[OP_COUNT] = {0, 1, 0, 1, 0};
+    for (int o = 0; o < OP_COUNT; ++o) {
+        const int dir = dirs[o];
+        LineOp& op = a.op[o];
+        std::memset(&op, 0, sizeof(op));
+        op.kind = a.kind;
+        op.N = a.N;
+        op.L = a.L;
+        op.group2 = a.group2;
+        op.dir = dir;
+        op.nin = dir == 0 ? a.lp : a.N;
+        op.nout = dir == 0 ? a.N : a.lp;
+        op.in_lo = a.lo;
+        op.out_lo = a.lo;
+        op.s_right = dir == 0 ? (a.bcr == PSTD_NEUMANN ? 1.0f : -1.0f)
+                              : (a.bcr == PSTD_NEUMANN ? -1.0f : 1.0f);
+        op.shift = a.d_shift;
+        op.fft = a.fft;
+        if (a.kind == 0) {
+            std::vector<float2> f(a.L);
+            for (int n = 0; n < a.L; ++n) {
+                std::complex<double> c = coeff(a, n, dir, scales[o]);
+                f[n] = make_float2((float)c.real(), (float)c.imag());
+            }
+            if ((rc = upload(f, &a.d_f[o])) != PSTD_OK) return rc;
+            op.f = a.d_f[o];
+        } else {
+            std::vector<float> D = dense_operator(a, dir, scales[o]);
+            if ((rc = upload(D, &a.d_dense[o])) != PSTD_OK) return rc;
+            op.dense = a.d_dense[o];
+        }
+    }
+
+    // lines of this axis: extents of p on the other axes
+    int64_t nl = 1, inner = 1;
+    for (int j = 0; j < P->ndim; ++j) {
+        if (j == i) continue;
+        nl *= P->shape[0][j];
+        if (j > i) inner *= P->shape[0][j];
+    }
+    a.nlines = nl;
+    a.inner = inner;
+    a.rs = a.lp > a.N ? a.lp : a.N;
+    int G = 16;
+    while (G > 2 && pstd::cta_smem_bytes(G, a.L, a.rs) > kSmemBudget) G -= 2;
+    if ((int64_t)G > nl) G = (int)nl;
+    if (G < 1) G = 1;
+    a.G = G;
+    a.smem = pstd::cta_smem_bytes(G, a.L, a.rs);
+    if (a.smem > 227 * 1024) return PSTD_EUNSUPPORTED;
+    return PSTD_OK;
+}
+
+void free_plan_memory(pstd_plan_s* P) {
+    for (auto& a : P->ax) {
+        cudaFree(a.d_tw);
+        cudaFree(a.d_shift);
+        for (int o = 0; o < OP_COUNT; ++o) {
+            cudaFree(a.d_f[o]);
+            cudaFree(a.d_dense[o]);
+        }
+    }
+    cudaFree(P->d_S);
+    for (auto& g : P->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+}
+
+int validate(const pstd_desc* d) {
+    if (!d || d->ndim < 1 || d->ndim > 3) return PSTD_EINVAL;
+    if (!(d->c0 > 0) || !(d->rho0 > 0) || !(d->dt > 0)) return PSTD_EINVAL;
+    if (!std::isfinite(d->c0) || !std::isfinite(d->rho0) || !std::isfinite(d->dt)) return PSTD_EINVAL;
+    if (d->uinit != PSTD_U_HALFSTEP && d->uinit != PSTD_U_AS_GIVEN) return PSTD_EINVAL;
+    for (int i = 0; i < d->ndim; ++i) {
+        if (d->ncells[i] < 1 || d->ncells[i] > (1 << 20)) return PSTD_EINVAL;
+        if (!(d->dx[i] > 0) || !std::isfinite(d->dx[i])) return PSTD_EINVAL;
+        for (int s = 0; s < 2; ++s)
+            if (d->bc[i][s] != PSTD_NEUMANN && d->bc[i][s] != PSTD_DIRICHLET) return PSTD_EINVAL;
+        if (d->ncells[i] == 1 && d->bc[i][0] == PSTD_DIRICHLET && d->bc[i][1] == PSTD_DIRICHLET)
+            return PSTD_EINVAL;
+    }
+    // leapfrog limit: c0 dt |k|_max / 2 <= 1 with the largest stored-mode
+    // wavenumber of each axis (NN keeps k = pi/dx; ND/DN pi(N-1/2)/L; DD pi(N-1)/L)
+    double k2 = 0;
+    for (int i = 0; i < d->ndim; ++i) {
+        const double N = (double)d->ncells[i], L = N * d->dx[i];
+        double kmax;
+        if (d->bc[i][0] == PSTD_NEUMANN && d->bc[i][1] == PSTD_NEUMANN) kmax = M_PI * N / L;
+        else if (d->bc[i][0] != d->bc[i][1]) kmax = M_PI * (N - 0.5) / L;
+        else kmax = M_PI * (N - 1.0) / L;
+        k2 += kmax * kmax;
+    }
+    if (d->c0 * d->dt * std::sqrt(k2) / 2.0 > 1.0) return PSTD_EUNSTABLE;
+    return PSTD_OK;
+}
+
+StepArgs step_args(pstd_plan_s* P, int a, float* p, float* const* u) {
+    Axis& A = P->ax[a];
+    StepArgs s;
+    s.opP = A.op[OP_STEP_P];
+    s.opU = A.op[OP_STEP_U];
+    s.nlines = A.nlines;
+    s.inner = A.inner;
+    s.G = A.G;
+    s.rs = A.rs;
+    s.p = p;
+    s.u = u[a];
+    const int d = P->ndim;
+    s.acc_in = (a == d - 1) ? p : P->d_S;
+    s.acc_out = (a == 0) ? p : P->d_S;
+    return s;
+}
+
+int launch_step(pstd_plan_s* P, float* p, float* const* u, int64_t* launches) {
+    for (int a = P->ndim - 1; a >= 0; --a) {
+        Axis& A = P->ax[a];
+        StepArgs s = step_args(P, a, p, u);
+        const unsigned grid = (unsigned)((A.nlines + A.G - 1) / A.G);
+        CK(pstd::launch_k_step(grid, A.smem, P->stream, s));
+        ++*launches;
+    }
+    return PSTD_OK;
+}
+
+int launch_grad(pstd_plan_s* P, int axis, int opi, const float* in, float* out, int acc) {
+    Axis& A = P->ax[axis];
+    GradArgs g;
+    g.op = A.op[opi];
+    g.nlines = A.nlines;
+    g.inner = A.inner;
+    g.G = A.G;
+    g.rs = A.rs;
+    g.in = in;
+    g.out = out;
+    g.accumulate = acc;
+    const unsigned grid = (unsigned)((A.nlines + A.G - 1) / A.G);
+    CK(pstd::launch_k_grad(grid, A.smem, P->stream, g));
+    return PSTD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pstd_version(void) { return "pstd-gb300 0.1 (sm_103a)"; }
+
+double pstd_dt_from_cfl(double cfl, double dx, double c0) { return cfl * dx / c0; }
+
+const char* pstd_strerror(int code) {
+    switch (code) {
+        case PSTD_OK: return "ok";
+        case PSTD_EINVAL: return "invalid argument";
+        case PSTD_EUNSTABLE: return "time step beyond the leapfrog stability limit";
+        case PSTD_ENOMEM: return "out of memory";
+        case PSTD_ECUDA: return "CUDA runtime error";
+        case PSTD_ETIMEOUT: return "device-side wait timed out";
+        case PSTD_EUNSUPPORTED: return "unsupported size";
+        default: return "unknown error";
+    }
+}
+
+const char* pstd_last_cuda_error(void) { return g_cuda_err.c_str(); }
+
+int pstd_plan(const pstd_desc* desc, void* stream, pstd_plan_t** out) {
+    if (!out) return PSTD_EINVAL;
+    *out = nullptr;
+    int rc = validate(desc);
+    if (rc != PSTD_OK) return rc;
+    pstd_plan_s* P = new (std::nothrow) pstd_plan_s();
+    if (!P) return PSTD_ENOMEM;
+    P->desc = *desc;
+    P->stream = (cudaStream_t)stream;
+    P->ndim = desc->ndim;
+    for (int f = 0; f < 4; ++f)
+        for (int j = 0; j < 3; ++j) P->shape[f][j] = 1;
+    for (int i = 0; i < P->ndim; ++i) {
+        const int64_t N = desc->ncells[i];
+        const int64_t lo = desc->bc[i][0] == PSTD_DIRICHLET ? 1 : 0;
+        const int64_t hi = desc->bc[i][1] == PSTD_DIRICHLET ? N - 1 : N;
+        P->shape[0][i] = hi - lo + 1;
+    }
+    for (int f = 1; f <= P->ndim; ++f) {
+        for (int j = 0; j < P->ndim; ++j) P->shape[f][j] = P->shape[0][j];
+        P->shape[f][f - 1] = desc->ncells[f - 1];
+    }
+    for (int i = 0; i < P->ndim && rc == PSTD_OK; ++i) rc = build_axis(P, i);
+    if (rc == PSTD_OK && P->ndim >= 2) {
+        cudaError_t e = cudaMalloc((void**)&P->d_S, (size_t)pstd_field_numel(P, 0) * sizeof(float));
+        if (e != cudaSuccess) rc = e == cudaErrorMemoryAllocation ? PSTD_ENOMEM : cuda_fail(e, "cudaMalloc(S)");
+    }
+    if (rc == PSTD_OK) {
+        size_t mx = 0;
+        for (int i = 0; i < P->ndim; ++i) mx = P->ax[i].smem > mx ? P->ax[i].smem : mx;
+        cudaError_t e = pstd::set_max_smem((int)mx);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaFuncSetAttribute");
+    }
+    if (rc != PSTD_OK) {
+        free_plan_memory(P);
+        delete P;
+        return rc;
+    }
+    *out = P;
+    return PSTD_OK;
+}
+
+int pstd_field_shape(const pstd_plan_t* P, int field, int64_t shape[3]) {
+    if (!P || !shape || field < 0 || field > P->ndim) return PSTD_EINVAL;
+    for (int j = 0; j < 3; ++j) shape[j] = P->shape[field][j];
+    return PSTD_OK;
+}
+
+int64_t pstd_field_numel(const pstd_plan_t* P, int field) {
+    if (!P || field < 0 || field > P->ndim) return 0;
+    return P->shape[field][0] * P->shape[field][1] * P->shape[field][2];
+}
+
+int pstd_grad(pstd_plan_t* P, int axis, int dir, const float* in, float* out) {
+    if (!P || axis < 0 || axis >= P->ndim || (dir != 0 && dir != 1) || !in || !out) return PSTD_EINVAL;
+    P->last_launches = 0;
+    int rc = launch_grad(P, axis, dir == 0 ? OP_GRAD_P : OP_GRAD_U, in, out, 0);
+    if (rc == PSTD_OK) P->last_launches = 1;
+    return rc;
+}
+
+int pstd_init_velocity(pstd_plan_t* P, const float* p0, float* const* u) {
+    if (!P || !p0 || !u) return PSTD_EINVAL;
+    for (int a = 0; a < P->ndim; ++a)
+        if (!u[a]) return PSTD_EINVAL;
+    P->last_launches = 0;
+    if (P->desc.uinit == PSTD_U_AS_GIVEN) return PSTD_OK;
+    for (int a = 0; a < P->ndim; ++a) {
+        int rc = launch_grad(P, a, OP_INIT_P, p0, u[a], 1);
+        if (rc != PSTD_OK) return rc;
+        ++P->last_launches;
+    }
+    return PSTD_OK;
+}
+
+int pstd_step(pstd_plan_t* P, float* p, float* const* u) {
+    if (!P || !p || !u) return PSTD_EINVAL;
+    for (int a = 0; a < P->ndim; ++a)
+        if (!u[a]) return PSTD_EINVAL;
+    P->last_launches = 0;
+    return launch_step(P, p, u, &P->last_launches);
+}
+
+int pstd_run(pstd_plan_t* P, float* p, float* const* u, int64_t nsteps) {
+    if (!P || !p || !u || nsteps < 0) return PSTD_EINVAL;
+    for (int a = 0; a < P->ndim; ++a)
+        if (!u[a]) return PSTD_EINVAL;
+    P->last_launches = 0;
+    int64_t done = 0;
+    if (P->stream != nullptr && nsteps >= kGraphSteps) {
+        // find or record the graph of kGraphSteps steps for this pointer set
+        GraphEntry* ge = nullptr;
+        for (auto& g : P->graphs) {
+            bool same = g.exec && g.p == p;
+            for (int a = 0; a < P->ndim && same; ++a) same = g.u[a] == u[a];
+            if (same) { ge = &g; break; }
+        }
+        if (!ge) {
+            GraphEntry* victim = &P->graphs[0];
+            for (auto& g : P->graphs) {
+                if (!g.exec) { victim = &g; break; }
+                if (g.stamp < victim->stamp) victim = &g;
+            }
+            if (victim->exec) { cudaGraphExecDestroy(victim->exec); victim->exec = nullptr; }
+            CK(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal));
+            int64_t nl = 0;
+            int rc = PSTD_OK;
+            for (int s = 0; s < kGraphSteps && rc == PSTD_OK; ++s) rc = launch_step(P, p, u, &nl);
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamEndCapture(P->stream, &graph);
+            if (rc != PSTD_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&victim->exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) { victim->exec = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+            victim->p = p;
+            for (int a = 0; a < 3; ++a) victim->u[a] = a < P->ndim ? u[a] : nullptr;
+            victim->steps = kGraphSteps;
+            victim->launches = nl;
+            ge = victim;
+        }
+        ge->stamp = ++P->stamp;
+        while (nsteps - done >= ge->steps) {
+            CK(cudaGraphLaunch(ge->exec, P->stream));
+            done += ge->steps;
+            P->last_launches += ge->launches;
+        }
+    }
+    while (done < nsteps) {
+        int rc = launch_step(P, p, u, &P->last_launches);
+        if (rc != PSTD_OK) return rc;
+        ++done;
+    }
+    return PSTD_OK;
+}
+
+int pstd_sync(pstd_plan_t* P) {
+    if (!P) return PSTD_EINVAL;
+    CK(cudaStreamSynchronize(P->stream));
+    CK(cudaGetLastError());
+    return PSTD_OK;
+}
+
+int pstd_free(pstd_plan_t* P) {
+    if (!P) return PSTD_OK;
+    cudaStreamSynchronize(P->stream);
+    free_plan_memory(P);
+    delete P;
+    return PSTD_OK;
+}
+
+int64_t pstd_last_launch_count(const pstd_plan_t* P) { return P ? P->last_launches : 0; }
+
+}  // extern "C"

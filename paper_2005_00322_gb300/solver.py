@@ -1,0 +1,146 @@
+"""Python binding of libpstd.so for torch device tensors (marshalling only).
+
+Every computation runs in the CUDA library; this module checks tensor
+arguments, passes raw device pointers and orders the plan's stream against
+torch's current stream.  It raises if the library is not built: there is no
+CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _abi
+
+_UINIT = {"halfstep": _abi.U_HALFSTEP, "as_given": _abi.U_AS_GIVEN}
+
+
+def stored_node_range(n: int, bc) -> tuple:
+    """(first, last) stored pressure node of an axis: Dirichlet wall nodes are dropped."""
+    lo = 1 if bc[0] in ("D", _abi.DIRICHLET) else 0
+    hi = n - 1 if bc[1] in ("D", _abi.DIRICHLET) else n
+    return lo, hi
+
+
+class Solver:
+    """A plan of the DTT-PSTD leapfrog on one GPU (see include/pstd.h).
+
+    ncells: cells per axis (1 to 3 axes); dx: spacing (scalar or per axis);
+    bc: per axis a (left, right) pair of "N" / "D"; dt or cfl (dt = cfl dx / c0
+    with the smallest dx); uinit: "halfstep" or "as_given".
+    """
+
+    def __init__(self, ncells, dx, bc, c0=1500.0, rho0=1000.0, dt=None, cfl=None,
+                 uinit="halfstep", device=None, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the PSTD library runs on the GPU only")
+        self.lib = _abi.load()
+        self.device = torch.device(device or "cuda", torch.cuda.current_device()
+                                   if device is None else torch.device(device).index)
+        self.ndim = len(ncells)
+        dxs = list(dx) if hasattr(dx, "__len__") else [dx] * self.ndim
+        if dt is None:
+            if cfl is None:
+                raise ValueError("give dt or cfl")
+            dt = self.lib.pstd_dt_from_cfl(float(cfl), float(min(dxs)), float(c0))
+        self.ncells, self.dx, self.bc = tuple(ncells), tuple(dxs), tuple(tuple(b) for b in bc)
+        self.c0, self.rho0, self.dt = float(c0), float(rho0), float(dt)
+        self._desc = _abi.make_desc(ncells, dxs, bc, c0, rho0, dt, _UINIT[uinit])
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        h = ctypes.c_void_p()
+        rc = self.lib.pstd_plan(ctypes.byref(self._desc), ctypes.c_void_p(self.stream.cuda_stream),
+                                ctypes.byref(h))
+        _abi.check(self.lib, rc, "pstd_plan")
+        self._h = h
+        self.shapes = [self.field_shape(f) for f in range(self.ndim + 1)]
+
+    # -- bookkeeping ---------------------------------------------------------
+    def field_shape(self, field: int) -> tuple:
+        s = (ctypes.c_int64 * 3)()
+        _abi.check(self.lib, self.lib.pstd_field_shape(self._h, field, s), "pstd_field_shape")
+        return tuple(int(s[i]) for i in range(self.ndim))
+
+    def zeros(self):
+        """Zero-filled (p, [u_1..u_d]) on the device."""
+        p = torch.zeros(self.shapes[0], dtype=torch.float32, device=self.device)
+        us = [torch.zeros(s, dtype=torch.float32, device=self.device) for s in self.shapes[1:]]
+        return p, us
+
+    def restrict(self, p_full):
+        """Stored pressure nodes of a field given on the full node lattice."""
+        sl = tuple(slice(*(lambda lo, hi: (lo, hi + 1))(*stored_node_range(n, b)))
+                   for n, b in zip(self.ncells, self.bc))
+        return p_full[sl]
+
+    def last_launch_count(self) -> int:
+        return int(self.lib.pstd_last_launch_count(self._h))
+
+    # -- argument checks -----------------------------------------------------
+    def _t(self, x, field: int, name: str):
+        if not isinstance(x, torch.Tensor):
+            raise TypeError(f"{name} must be a torch tensor")
+        if x.device != self.device or x.dtype != torch.float32 or not x.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float32 tensor on {self.device}")
+        if tuple(x.shape) != self.shapes[field]:
+            raise ValueError(f"{name} has shape {tuple(x.shape)}, expected {self.shapes[field]}")
+        return ctypes.c_void_p(x.data_ptr())
+
+    def _us(self, us):
+        if len(us) != self.ndim:
+            raise ValueError(f"expected {self.ndim} velocity fields")
+        arr = (ctypes.c_void_p * 3)()
+        for i, u in enumerate(us):
+            arr[i] = self._t(u, i + 1, f"u[{i}]")
+        return arr
+
+    def _enter(self):
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+
+    def _leave(self):
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+
+    # -- the C ABI -----------------------------------------------------------
+    def grad(self, axis: int, direction: int, x, out=None):
+        """Staggered derivative along ``axis``: direction 0 p -> u_axis, 1 u_axis -> p."""
+        fin, fout = (0, axis + 1) if direction == 0 else (axis + 1, 0)
+        if out is None:
+            out = torch.empty(self.shapes[fout], dtype=torch.float32, device=self.device)
+        a, b = self._t(x, fin, "in"), self._t(out, fout, "out")
+        self._enter()
+        _abi.check(self.lib, self.lib.pstd_grad(self._h, axis, direction, a, b), "pstd_grad")
+        self._leave()
+        return out
+
+    def init_velocity(self, p0, us):
+        a, arr = self._t(p0, 0, "p0"), self._us(us)
+        self._enter()
+        _abi.check(self.lib, self.lib.pstd_init_velocity(self._h, a, arr), "pstd_init_velocity")
+        self._leave()
+
+    def step(self, p, us):
+        a, arr = self._t(p, 0, "p"), self._us(us)
+        self._enter()
+        _abi.check(self.lib, self.lib.pstd_step(self._h, a, arr), "pstd_step")
+        self._leave()
+
+    def run(self, p, us, nsteps: int):
+        a, arr = self._t(p, 0, "p"), self._us(us)
+        self._enter()
+        _abi.check(self.lib, self.lib.pstd_run(self._h, a, arr, int(nsteps)), "pstd_run")
+        self._leave()
+
+    def sync(self):
+        _abi.check(self.lib, self.lib.pstd_sync(self._h), "pstd_sync")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.pstd_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
