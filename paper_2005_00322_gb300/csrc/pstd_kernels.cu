@@ -28,8 +28,17 @@ cudaError_t launch_k_grad(unsigned grid, size_t smem, cudaStream_t st, const Gra
     return cudaGetLastError();
 }
 
+// Raise the kernels' dynamic shared-memory limit to the device's opt-in
+// maximum (never lowered, so plans with different needs coexist).
 cudaError_t set_max_smem(int bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (bytes > optin) return cudaErrorInvalidValue;
+    bytes = optin;
+    e = cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
