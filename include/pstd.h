@@ -148,6 +148,35 @@ int64_t pstd_last_launch_count(const pstd_plan_t* plan);
 /* Library version string. */
 const char* pstd_version(void);
 
+/* Capacity of pstd_step_noalloc: pressure points, and FFT length 2 N_i per axis. */
+#define PSTD_NOALLOC_MAX_POINTS (1 << 22)
+#define PSTD_NOALLOC_MAX_FFT 4096
+
+/* `nsteps` >= 0 leapfrog steps in place, like pstd_plan + pstd_run + pstd_free,
+ * but without allocating anything: no cudaMalloc, cudaFree or allocating
+ * library call, host or device.  The paper has no counterpart; this exists for
+ * callers that must not allocate device memory when they call us -- a host
+ * application whose device memory belongs to a memory manager (a framework's
+ * caching allocator, or a budget fixed at start-up) that forbids allocations
+ * it does not make, or a latency-critical loop that cannot pay for cudaMalloc
+ * and cudaFree, which may synchronise the device.
+ * The caller passes the descriptor, p and the ndim velocity fields (device
+ * pointers, the layout of pstd_field_shape) and a cudaStream_t (NULL = legacy
+ * default stream).  The scratch accumulator and the coefficient tables live in
+ * fixed file-scope device arrays (16 MiB + 384 KiB, held on every GPU that
+ * loads the library until the process exits); each call recomputes the tables
+ * in FP64 on the device.  The first call on a device also resolves those
+ * arrays' device addresses (with that device current); make that first call
+ * before any stream capture.  All calls share the arrays: calls whose work
+ * overlaps on the GPU race, so serialise them (one stream, one host thread).
+ * Only axes whose 2 N_i factors into 2, 3 and 5 are supported, with
+ * 2 N_i <= PSTD_NOALLOC_MAX_FFT and at most PSTD_NOALLOC_MAX_POINTS pressure
+ * points; larger or other sizes return PSTD_EUNSUPPORTED before any device
+ * work.  u^{-1/2} must already be in u (see pstd_init_velocity).
+ * Errors: PSTD_EINVAL, PSTD_EUNSTABLE, PSTD_EUNSUPPORTED, PSTD_ECUDA. */
+int pstd_step_noalloc(const pstd_desc* desc, float* p, float* const* u, int64_t nsteps,
+                      void* stream);
+
 #ifdef __cplusplus
 }
 #endif

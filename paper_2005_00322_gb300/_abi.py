@@ -30,6 +30,7 @@ SIGNATURES = {
     "pstd_dt_from_cfl": (c_double, [c_double, c_double, c_double]),
     "pstd_last_launch_count": (c_int64, [c_void_p]),
     "pstd_version": (c_char_p, []),
+    "pstd_step_noalloc": (c_int, [c_void_p, c_void_p, POINTER(c_void_p), c_int64, c_void_p]),
 }
 
 
