@@ -24,18 +24,36 @@
 
 #include "../../include/pstd.h"
 #include "pstd_cta.cuh"
+#include "pstd_wkernels.cuh"
 
 namespace pstd {
 // Launchers and attribute setup, defined with the kernels (pstd_kernels.cu).
 cudaError_t launch_k_step(unsigned grid, size_t smem, cudaStream_t st, const StepArgs& a);
 cudaError_t launch_k_grad(unsigned grid, size_t smem, cudaStream_t st, const GradArgs& a);
 cudaError_t set_max_smem(int bytes);
+// register-FFT passes, one dispatcher per translation unit (pstd_wkernels_*.cu)
+cudaError_t wsmall_step(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WStep& a);
+cudaError_t wsmall_grad(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WGrad& a);
+cudaError_t wsmall_smem(int L, int V, int bytes);
+bool wsmall_twiddles(int L, int V, std::vector<float2>& out);
+cudaError_t w512_step(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WStep& a);
+cudaError_t w512_grad(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WGrad& a);
+cudaError_t w512_smem(int L, int V, int bytes);
+bool w512_twiddles(int L, int V, std::vector<float2>& out);
+cudaError_t w1024_step(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WStep& a);
+cudaError_t w1024_grad(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WGrad& a);
+cudaError_t w1024_smem(int L, int V, int bytes);
+bool w1024_twiddles(int L, int V, std::vector<float2>& out);
 }  // namespace pstd
 
 using pstd::FftPlan;
 using pstd::GradArgs;
 using pstd::LineOp;
 using pstd::StepArgs;
+using pstd::WAxis;
+using pstd::WGrad;
+using pstd::WLaunch;
+using pstd::WStep;
 
 namespace {
 
@@ -62,7 +80,35 @@ struct Axis {
     int64_t nlines = 0, inner = 1;
     int G = 2, rs = 1;
     size_t smem = 0;
+    // register-FFT passes (wl > 0: lanes per sequence)
+    int wl = 0, wv = 0;
+    bool strided = false;
+    float2* d_wtw = nullptr;
+    WAxis wax{};
+    WLaunch wgeo{};
 };
+
+// register-FFT dispatch by length and schedule variant
+cudaError_t wstep(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WStep& a) {
+    if (L >= 1024 || L == 768) return pstd::w1024_step(L, V, s, g, st, a);
+    if (L == 512 || L == 384) return pstd::w512_step(L, V, s, g, st, a);
+    return pstd::wsmall_step(L, V, s, g, st, a);
+}
+cudaError_t wgrad(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WGrad& a) {
+    if (L >= 1024 || L == 768) return pstd::w1024_grad(L, V, s, g, st, a);
+    if (L == 512 || L == 384) return pstd::w512_grad(L, V, s, g, st, a);
+    return pstd::wsmall_grad(L, V, s, g, st, a);
+}
+cudaError_t wsmem(int L, int V, int bytes) {
+    if (L >= 1024 || L == 768) return pstd::w1024_smem(L, V, bytes);
+    if (L == 512 || L == 384) return pstd::w512_smem(L, V, bytes);
+    return pstd::wsmall_smem(L, V, bytes);
+}
+bool wtw(int L, int V, std::vector<float2>& out) {
+    if (L >= 1024 || L == 768) return pstd::w1024_twiddles(L, V, out);
+    if (L == 512 || L == 384) return pstd::w512_twiddles(L, V, out);
+    return pstd::wsmall_twiddles(L, V, out);
+}
 
 struct GraphEntry {
     float* p = nullptr;
@@ -282,6 +328,58 @@ int build_axis(pstd_plan_s* P, int i) {
     a.G = G;
     a.smem = pstd::cta_smem_bytes(G, a.L, a.rs);
     if (a.smem > 227 * 1024) return PSTD_EUNSUPPORTED;
+
+    // register-FFT passes where a schedule exists; an axis with too few line
+    // pairs to fill the GPU (4 per SM) takes the latency schedule
+    int T = pstd::wlanes(a.L);
+    int V = 0;
+    if (pstd::wlanes_latency(a.L) > 0 && (a.nlines + 1) / 2 < 4 * 152) {
+        V = 1;
+        T = pstd::wlanes_latency(a.L);
+    }
+    if (a.kind == 0 && T > 0) {
+        std::vector<float2> wt;
+        if (!wtw(a.L, V, wt)) return PSTD_EUNSUPPORTED;
+        if ((rc = upload(wt, &a.d_wtw)) != PSTD_OK) return rc;
+        WAxis& w = a.wax;
+        w.N = a.N;
+        w.L = a.L;
+        w.lp = a.lp;
+        w.lo = a.lo;
+        w.group2 = a.group2;
+        w.sR_p = a.bcr == PSTD_NEUMANN ? 1.0f : -1.0f;
+        w.sR_u = a.bcr == PSTD_NEUMANN ? -1.0f : 1.0f;
+        w.tw = a.d_wtw;
+        w.shift = a.d_shift;
+        w.nlines = a.nlines;
+        w.inner = a.inner;
+        a.strided = a.inner > 1;
+        const int64_t nseq = (a.nlines + 1) / 2;
+        const int64_t want = 2 * 152;
+        int threads = 128;
+        if (!a.strided) {
+            while (threads > 32 && threads > T && (nseq * T + threads - 1) / threads < want) threads /= 2;
+            w.seqs = threads / T;
+            w.G = 2 * w.seqs;
+            a.wgeo.grid = (unsigned)((nseq + w.seqs - 1) / w.seqs);
+            a.wgeo.smem = (size_t)w.seqs * pstd::wseq_words(a.L) * sizeof(float2);
+        } else {
+            const int64_t outer = a.nlines / a.inner;
+            auto tiles = [&](int th) {
+                const int G2 = 2 * (th / T);
+                return outer * ((a.inner + G2 - 1) / G2);
+            };
+            while (threads > 32 && threads > T && tiles(threads) < want) threads /= 2;
+            w.seqs = threads / T;
+            w.G = 2 * w.seqs;
+            a.wgeo.grid = (unsigned)tiles(threads);
+            a.wgeo.smem = pstd::wk::strided_step_floats(w, pstd::wseq_words(a.L), true) * sizeof(float);
+        }
+        a.wgeo.threads = threads;
+        if (a.wgeo.smem > 200 * 1024) return PSTD_EUNSUPPORTED;
+        a.wl = T;
+        a.wv = V;
+    }
     return PSTD_OK;
 }
 
@@ -289,6 +387,7 @@ void free_plan_memory(pstd_plan_s* P) {
     for (auto& a : P->ax) {
         cudaFree(a.d_tw);
         cudaFree(a.d_shift);
+        cudaFree(a.d_wtw);
         for (int o = 0; o < OP_COUNT; ++o) {
             cudaFree(a.d_f[o]);
             cudaFree(a.d_dense[o]);
@@ -347,6 +446,19 @@ StepArgs step_args(pstd_plan_s* P, int a, float* p, float* const* u) {
 int launch_step(pstd_plan_s* P, float* p, float* const* u, int64_t* launches) {
     for (int a = P->ndim - 1; a >= 0; --a) {
         Axis& A = P->ax[a];
+        if (A.wl) {
+            WStep w;
+            w.ax = A.wax;
+            w.fP = A.d_f[OP_STEP_P];
+            w.fU = A.d_f[OP_STEP_U];
+            w.p = p;
+            w.u = u[a];
+            w.acc_in = (a == P->ndim - 1) ? p : P->d_S;
+            w.acc_out = (a == 0) ? p : P->d_S;
+            CK(wstep(A.L, A.wv, A.strided, A.wgeo, P->stream, w));
+            ++*launches;
+            continue;
+        }
         StepArgs s = step_args(P, a, p, u);
         const unsigned grid = (unsigned)((A.nlines + A.G - 1) / A.G);
         CK(pstd::launch_k_step(grid, A.smem, P->stream, s));
@@ -357,6 +469,17 @@ int launch_step(pstd_plan_s* P, float* p, float* const* u, int64_t* launches) {
 
 int launch_grad(pstd_plan_s* P, int axis, int opi, const float* in, float* out, int acc) {
     Axis& A = P->ax[axis];
+    if (A.wl) {
+        WGrad g;
+        g.ax = A.wax;
+        g.dir = A.op[opi].dir;
+        g.f = A.d_f[opi];
+        g.in = in;
+        g.out = out;
+        g.accumulate = acc;
+        CK(wgrad(A.L, A.wv, A.strided, A.wgeo, P->stream, g));
+        return PSTD_OK;
+    }
     GradArgs g;
     g.op = A.op[opi];
     g.nlines = A.nlines;
@@ -426,6 +549,14 @@ int pstd_plan(const pstd_desc* desc, void* stream, pstd_plan_t** out) {
         for (int i = 0; i < P->ndim; ++i) mx = P->ax[i].smem > mx ? P->ax[i].smem : mx;
         cudaError_t e = pstd::set_max_smem((int)mx);
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaFuncSetAttribute");
+        for (int i = 0; i < P->ndim && rc == PSTD_OK; ++i) {
+            if (!P->ax[i].wl) continue;
+            int dev = 0, optin = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            e = wsmem(P->ax[i].L, P->ax[i].wv, optin);
+            if (e != cudaSuccess) rc = cuda_fail(e, "cudaFuncSetAttribute(register-FFT pass)");
+        }
     }
     if (rc != PSTD_OK) {
         free_plan_memory(P);

@@ -1,0 +1,118 @@
+// pstd_wkernels.cuh -- kernels of the register-FFT axis passes, templated on
+// the FFT length L, and their launchers.  Each .cu file that includes this
+// header instantiates one group of lengths (see pstd_wkernels_*.cu).
+#pragma once
+
+#include <vector>
+
+#include "pstd_wcta.cuh"
+
+namespace pstd {
+
+template <int L, int V>
+__global__ void __launch_bounds__(256) k_wstep_c(WStep a) {
+    extern __shared__ float2 wsm[];
+    wk::step_contig<wf::Sched<L, V>>(a, blockIdx.x, wsm, threadIdx.x);
+}
+template <int L, int V>
+__global__ void __launch_bounds__(256) k_wstep_s(WStep a) {
+    extern __shared__ float2 wsm[];
+    wk::step_strided<wf::Sched<L, V>>(a, blockIdx.x, wsm, threadIdx.x, blockDim.x);
+}
+template <int L, int V>
+__global__ void __launch_bounds__(256) k_wgrad_c(WGrad a) {
+    extern __shared__ float2 wsm[];
+    wk::grad_contig<wf::Sched<L, V>>(a, blockIdx.x, wsm, threadIdx.x);
+}
+template <int L, int V>
+__global__ void __launch_bounds__(256) k_wgrad_s(WGrad a) {
+    extern __shared__ float2 wsm[];
+    wk::grad_strided<wf::Sched<L, V>>(a, blockIdx.x, wsm, threadIdx.x, blockDim.x);
+}
+
+// Launch geometry shared by the host plan and the launchers.
+struct WLaunch {
+    unsigned grid;
+    int threads;
+    size_t smem;
+};
+
+template <int L, int V>
+cudaError_t wlaunch_step(bool strided, const WLaunch& g, cudaStream_t st, const WStep& a) {
+    if (strided) k_wstep_s<L, V><<<g.grid, g.threads, g.smem, st>>>(a);
+    else k_wstep_c<L, V><<<g.grid, g.threads, g.smem, st>>>(a);
+    return cudaGetLastError();
+}
+template <int L, int V>
+cudaError_t wlaunch_grad(bool strided, const WLaunch& g, cudaStream_t st, const WGrad& a) {
+    if (strided) k_wgrad_s<L, V><<<g.grid, g.threads, g.smem, st>>>(a);
+    else k_wgrad_c<L, V><<<g.grid, g.threads, g.smem, st>>>(a);
+    return cudaGetLastError();
+}
+template <int L, int V>
+cudaError_t wset_smem(int bytes) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_wstep_s<L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+    if ((e = cudaFuncSetAttribute(k_wstep_c<L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+    if ((e = cudaFuncSetAttribute(k_wgrad_s<L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+    return cudaFuncSetAttribute(k_wgrad_c<L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+// pass twiddles of Sched<L, V>, FP64 angles rounded once
+template <int L, int V>
+void wtwiddles(std::vector<float2>& out) {
+    using S = wf::Sched<L, V>;
+    out.assign(wf::tw_total<S>() > 0 ? wf::tw_total<S>() : 1, make_float2(1.0f, 0.0f));
+    wf::fill_pass_twiddles<S>([&](int idx, long m, long n) {
+        const double ang = 2.0 * wf::kPi * (double)m / (double)n;
+        out[idx] = make_float2((float)cos(ang), (float)-sin(ang));
+    });
+}
+
+// Dispatch over the (length, variant) pairs one translation unit
+// instantiates; the key is 2 L + V.
+#define PSTD_WDISPATCH(NAME, LIST)                                                                        \
+    cudaError_t NAME##_step(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WStep& a) {   \
+        switch (2 * L + V) { LIST(PSTD_WCASE_STEP) default: return cudaErrorInvalidValue; }              \
+    }                                                                                                    \
+    cudaError_t NAME##_grad(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WGrad& a) {   \
+        switch (2 * L + V) { LIST(PSTD_WCASE_GRAD) default: return cudaErrorInvalidValue; }              \
+    }                                                                                                    \
+    cudaError_t NAME##_smem(int L, int V, int bytes) {                                                   \
+        switch (2 * L + V) { LIST(PSTD_WCASE_SMEM) default: return cudaErrorInvalidValue; }              \
+    }                                                                                                    \
+    bool NAME##_twiddles(int L, int V, std::vector<float2>& out) {                                       \
+        switch (2 * L + V) { LIST(PSTD_WCASE_TW) default: return false; }                                \
+    }
+#define PSTD_WCASE_STEP(LL, VV) case 2 * LL + VV: return wlaunch_step<LL, VV>(s, g, st, a);
+#define PSTD_WCASE_GRAD(LL, VV) case 2 * LL + VV: return wlaunch_grad<LL, VV>(s, g, st, a);
+#define PSTD_WCASE_SMEM(LL, VV) case 2 * LL + VV: return wset_smem<LL, VV>(bytes);
+#define PSTD_WCASE_TW(LL, VV) case 2 * LL + VV: wtwiddles<LL, VV>(out); return true;
+
+// Lanes per sequence of the latency schedule Sched<L, 1> (0: none).
+inline int wlanes_latency(int L) {
+    switch (L) {
+        case 256: return 32;
+        case 512: return 64;
+        case 1024: return 128;
+        default: return 0;
+    }
+}
+
+// Lanes per sequence of Sched<L, 0> (0: not instantiated).
+inline int wlanes(int L) {
+    switch (L) {
+        case 2: case 4: case 8: case 16: case 32: return 1;
+        case 64: return 4;
+        case 128: return 8;
+        case 256: case 512: return 16;
+        case 1024: return 32;
+        case 96: return 4;
+        case 192: return 8;
+        case 384: return 16;
+        case 768: return 32;
+        default: return 0;
+    }
+}
+inline int wseq_words(int L) { return L + L / 32 + 1; }
+
+}  // namespace pstd

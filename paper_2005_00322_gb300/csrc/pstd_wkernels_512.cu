@@ -1,0 +1,7 @@
+// Register-FFT axis passes for FFT lengths 512 and 384.
+#include <cmath>
+#include "pstd_wkernels.cuh"
+namespace pstd {
+#define PSTD_WLIST_512(X) X(512, 0) X(384, 0) X(512, 1)
+PSTD_WDISPATCH(w512, PSTD_WLIST_512)
+}  // namespace pstd

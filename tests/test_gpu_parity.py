@@ -49,6 +49,8 @@ CASES = [
     ((30, 45), [("N", "D"), ("D", "N")]),
     ((24, 20, 18), [("D", "N"), ("N", "N"), ("D", "D")]),
     ((16, 27, 25), [("N", "N"), ("D", "D"), ("N", "D")]),
+    ((192, 20), [("D", "N"), ("N", "N")]), ((8, 96), [("N", "D"), ("D", "D")]),
+    ((512, 6), [("N", "N"), ("D", "N")]), ((3, 384), [("D", "D"), ("N", "D")]),
     # dense route (2N has a factor 7, 11 or 13) and tiny edge sizes
     ((7,), [("N", "D")]), ((11,), [("D", "D")]), ((13, 6), [("N", "N"), ("D", "N")]),
     ((1,), [("N", "N")]), ((1,), [("N", "D")]), ((2,), [("D", "D")]), ((2, 3), [("D", "N"), ("N", "D")]),
