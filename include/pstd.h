@@ -94,6 +94,26 @@ typedef struct pstd_plan_s pstd_plan_t;
  * PSTD_EUNSUPPORTED, PSTD_ENOMEM, PSTD_ECUDA.  *out is NULL on error. */
 int pstd_plan(const pstd_desc* desc, void* stream, pstd_plan_t** out);
 
+/* Launch schedule of each axis pass, for tuning; -1 leaves a choice to the
+ * plan.  variant 0 keeps many elements per lane and few FFT passes (for axes
+ * with many lines), variant 1 spreads each FFT over up to 128 lanes (for
+ * axes with too few lines to fill the GPU; FFT lengths 256, 512, 1024 only).
+ * seqs_per_cta: line pairs per CTA (a power of two). */
+typedef struct {
+    int variant[3];
+    int seqs_per_cta[3];
+} pstd_plan_opts;
+
+/* pstd_plan with explicit schedule options (NULL = all automatic).
+ * Errors: those of pstd_plan; PSTD_EINVAL for an option the axis cannot use. */
+int pstd_plan_ex(const pstd_desc* desc, void* stream, const pstd_plan_opts* opts,
+                 pstd_plan_t** out);
+
+/* The schedule a plan chose for `axis`: variant, lanes per sequence,
+ * sequences per CTA, CTAs per launch (-1 for an axis on the generic
+ * shared-memory FFT or dense path).  Errors: PSTD_EINVAL. */
+int pstd_plan_schedule(const pstd_plan_t* plan, int axis, int out[4]);
+
 /* Shape of field 0 (p) or field i+1 (u_i) as three extents (unused axes 1).
  * Errors: PSTD_EINVAL. */
 int pstd_field_shape(const pstd_plan_t* plan, int field, int64_t shape[3]);

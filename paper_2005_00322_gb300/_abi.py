@@ -17,6 +17,8 @@ ERRORS = {0: "PSTD_OK", -1: "PSTD_EINVAL", -2: "PSTD_EUNSTABLE", -3: "PSTD_ENOME
 # Every symbol include/pstd.h declares, with (restype, argtypes).
 SIGNATURES = {
     "pstd_plan": (c_int, [c_void_p, c_void_p, POINTER(c_void_p)]),
+    "pstd_plan_ex": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(c_void_p)]),
+    "pstd_plan_schedule": (c_int, [c_void_p, c_int, POINTER(c_int)]),
     "pstd_field_shape": (c_int, [c_void_p, c_int, POINTER(c_int64)]),
     "pstd_field_numel": (c_int64, [c_void_p, c_int]),
     "pstd_grad": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
@@ -46,6 +48,11 @@ class PstdDesc(ctypes.Structure):
         ("dt", c_double),
         ("uinit", c_int),
     ]
+
+
+class PstdPlanOpts(ctypes.Structure):
+    """Mirror of pstd_plan_opts (-1 = automatic)."""
+    _fields_ = [("variant", c_int * 3), ("seqs_per_cta", c_int * 3)]
 
 
 class PstdError(RuntimeError):

@@ -159,6 +159,7 @@ bool radix_schedule(int L, FftPlan& P) {
 
 struct pstd_plan_s {
     pstd_desc desc{};
+    pstd_plan_opts opts{{-1, -1, -1}, {-1, -1, -1}};
     cudaStream_t stream = nullptr;
     int ndim = 0;
     int64_t shape[4][3] = {};
@@ -333,10 +334,13 @@ int build_axis(pstd_plan_s* P, int i) {
     // pairs to fill the GPU (4 per SM) takes the latency schedule
     int T = pstd::wlanes(a.L);
     int V = 0;
-    if (pstd::wlanes_latency(a.L) > 0 && (a.nlines + 1) / 2 < 4 * 152) {
+    const int ov = P->opts.variant[i], os = P->opts.seqs_per_cta[i];
+    if (ov == 1 || (ov < 0 && pstd::wlanes_latency(a.L) > 0 && (a.nlines + 1) / 2 < 4 * 152)) {
+        if (pstd::wlanes_latency(a.L) == 0) return PSTD_EINVAL;
         V = 1;
         T = pstd::wlanes_latency(a.L);
     }
+    if (os == 0 || os > 256 || (os > 0 && (os & (os - 1)))) return PSTD_EINVAL;
     if (a.kind == 0 && T > 0) {
         std::vector<float2> wt;
         if (!wtw(a.L, V, wt)) return PSTD_EUNSUPPORTED;
@@ -356,24 +360,31 @@ int build_axis(pstd_plan_s* P, int i) {
         a.strided = a.inner > 1;
         const int64_t nseq = (a.nlines + 1) / 2;
         const int64_t want = 2 * 152;
-        int threads = 128;
+        int threads = V == 1 ? T : 128;
+        if (os > 0) {
+            threads = os * T;
+            if (threads < 32 || threads > 256) return PSTD_EINVAL;
+        }
         if (!a.strided) {
-            while (threads > 32 && threads > T && (nseq * T + threads - 1) / threads < want) threads /= 2;
+            while (os < 0 && threads > 32 && threads > T && (nseq * T + threads - 1) / threads < want)
+                threads /= 2;
             w.seqs = threads / T;
             w.G = 2 * w.seqs;
             a.wgeo.grid = (unsigned)((nseq + w.seqs - 1) / w.seqs);
             a.wgeo.smem = (size_t)w.seqs * pstd::wseq_words(a.L) * sizeof(float2);
+            a.wgeo.smem += (wt.size() + 3 * (size_t)a.L) * sizeof(float2);   // staged tables
         } else {
             const int64_t outer = a.nlines / a.inner;
             auto tiles = [&](int th) {
                 const int G2 = 2 * (th / T);
                 return outer * ((a.inner + G2 - 1) / G2);
             };
-            while (threads > 32 && threads > T && tiles(threads) < want) threads /= 2;
+            while (os < 0 && threads > 32 && threads > T && tiles(threads) < want) threads /= 2;
             w.seqs = threads / T;
             w.G = 2 * w.seqs;
             a.wgeo.grid = (unsigned)tiles(threads);
             a.wgeo.smem = pstd::wk::strided_step_floats(w, pstd::wseq_words(a.L), true) * sizeof(float);
+            a.wgeo.smem += (wt.size() + 3 * (size_t)a.L) * sizeof(float2);   // staged tables
         }
         a.wgeo.threads = threads;
         if (a.wgeo.smem > 200 * 1024) return PSTD_EUNSUPPORTED;
@@ -518,6 +529,24 @@ const char* pstd_strerror(int code) {
 const char* pstd_last_cuda_error(void) { return g_cuda_err.c_str(); }
 
 int pstd_plan(const pstd_desc* desc, void* stream, pstd_plan_t** out) {
+    return pstd_plan_ex(desc, stream, nullptr, out);
+}
+
+int pstd_plan_schedule(const pstd_plan_t* P, int axis, int out[4]) {
+    if (!P || !out || axis < 0 || axis >= P->ndim) return PSTD_EINVAL;
+    const Axis& A = P->ax[axis];
+    if (!A.wl) {
+        out[0] = out[1] = out[2] = out[3] = -1;
+        return PSTD_OK;
+    }
+    out[0] = A.wv;
+    out[1] = A.wl;
+    out[2] = A.wax.seqs;
+    out[3] = (int)A.wgeo.grid;
+    return PSTD_OK;
+}
+
+int pstd_plan_ex(const pstd_desc* desc, void* stream, const pstd_plan_opts* opts, pstd_plan_t** out) {
     if (!out) return PSTD_EINVAL;
     *out = nullptr;
     int rc = validate(desc);
@@ -525,6 +554,7 @@ int pstd_plan(const pstd_desc* desc, void* stream, pstd_plan_t** out) {
     pstd_plan_s* P = new (std::nothrow) pstd_plan_s();
     if (!P) return PSTD_ENOMEM;
     P->desc = *desc;
+    if (opts) P->opts = *opts;
     P->stream = (cudaStream_t)stream;
     P->ndim = desc->ndim;
     for (int f = 0; f < 4; ++f)

@@ -178,13 +178,14 @@ PSTD_HD int pad(int i) { return i + (i >> 5); }
 template <int L>
 constexpr int seq_words() { return L + L / 32 + 1; }
 
-// Butterflies of pass p for lane t (in registers, outputs in place).
-template <class S, int p, bool INV>
-PSTD_HD void pass_compute(float2 (&v)[S::E], int t, const float2* tw) {
+// Butterflies of pass p for lane t (in registers, outputs in place).  The
+// inter-pass twiddles come from `tw(i)`: entry i of this lane's slice of the
+// pass tables, i = tw_offset<S, p>() / T + bm (R - 1) + (k - 1).
+template <class S, int p, bool INV, class Tw>
+PSTD_HD void pass_compute(float2 (&v)[S::E], Tw&& tw) {
     constexpr int E = S::E, T = S::T, R = S::R[p], B = E / R;
     constexpr int Ns = span_before<S, p>();
-    constexpr int L = S::L;
-    const float2* twp = tw + tw_offset<S, p>();
+    constexpr int base = tw_offset<S, p>() / T;
 #pragma unroll
     for (int b = 0; b < B; ++b) {
         float2 a[R];
@@ -195,7 +196,7 @@ PSTD_HD void pass_compute(float2 (&v)[S::E], int t, const float2* tw) {
             const int bm = b % BM;
 #pragma unroll
             for (int k = 1; k < R; ++k) {
-                float2 w = PSTD_LDG(&twp[(bm * (R - 1) + (k - 1)) * T + t]);
+                float2 w = tw(base + bm * (R - 1) + (k - 1));
                 if (INV) w.y = -w.y;
                 a[k] = cmul(a[k], w);
             }
@@ -204,8 +205,11 @@ PSTD_HD void pass_compute(float2 (&v)[S::E], int t, const float2* tw) {
 #pragma unroll
         for (int k = 0; k < R; ++k) v[b + k * B] = a[k];
     }
-    (void)L;
 }
+
+// Entries of one lane's slice of the pass tables (tw_total is a multiple of T).
+template <class S>
+constexpr int tw_per_lane() { return tw_total<S>() / S::T; }
 
 // Scatter pass p's outputs (not the last pass) into the sequence buffer.
 template <class S, int p>

@@ -11,22 +11,26 @@ namespace pstd {
 
 template <int L, int V>
 __global__ void __launch_bounds__(256) k_wstep_c(WStep a) {
-    extern __shared__ float2 wsm[];
-    wk::step_contig<wf::Sched<L, V>>(a, blockIdx.x, wsm, threadIdx.x);
+    extern __shared__ float4 wsm4[];  // 16-byte aligned for cp.async
+    float2* wsm = (float2*)wsm4;
+    wk::step_contig<wf::Sched<L, V>>(a, blockIdx.x, wsm, threadIdx.x, blockDim.x);
 }
 template <int L, int V>
 __global__ void __launch_bounds__(256) k_wstep_s(WStep a) {
-    extern __shared__ float2 wsm[];
+    extern __shared__ float4 wsm4[];  // 16-byte aligned for cp.async
+    float2* wsm = (float2*)wsm4;
     wk::step_strided<wf::Sched<L, V>>(a, blockIdx.x, wsm, threadIdx.x, blockDim.x);
 }
 template <int L, int V>
 __global__ void __launch_bounds__(256) k_wgrad_c(WGrad a) {
-    extern __shared__ float2 wsm[];
-    wk::grad_contig<wf::Sched<L, V>>(a, blockIdx.x, wsm, threadIdx.x);
+    extern __shared__ float4 wsm4[];  // 16-byte aligned for cp.async
+    float2* wsm = (float2*)wsm4;
+    wk::grad_contig<wf::Sched<L, V>>(a, blockIdx.x, wsm, threadIdx.x, blockDim.x);
 }
 template <int L, int V>
 __global__ void __launch_bounds__(256) k_wgrad_s(WGrad a) {
-    extern __shared__ float2 wsm[];
+    extern __shared__ float4 wsm4[];  // 16-byte aligned for cp.async
+    float2* wsm = (float2*)wsm4;
     wk::grad_strided<wf::Sched<L, V>>(a, blockIdx.x, wsm, threadIdx.x, blockDim.x);
 }
 
@@ -61,7 +65,9 @@ cudaError_t wset_smem(int bytes) {
 template <int L, int V>
 void wtwiddles(std::vector<float2>& out) {
     using S = wf::Sched<L, V>;
-    out.assign(wf::tw_total<S>() > 0 ? wf::tw_total<S>() : 1, make_float2(1.0f, 0.0f));
+    // even length (16-byte copies), at least one pair
+    const int n = (wf::tw_total<S>() + 1) & ~1;
+    out.assign(n > 0 ? n : 2, make_float2(1.0f, 0.0f));
     wf::fill_pass_twiddles<S>([&](int idx, long m, long n) {
         const double ang = 2.0 * wf::kPi * (double)m / (double)n;
         out[idx] = make_float2((float)cos(ang), (float)-sin(ang));

@@ -32,7 +32,7 @@ class Solver:
     """
 
     def __init__(self, ncells, dx, bc, c0=1500.0, rho0=1000.0, dt=None, cfl=None,
-                 uinit="halfstep", device=None, stream=None):
+                 uinit="halfstep", device=None, stream=None, schedule=None):
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the PSTD library runs on the GPU only")
         self.lib = _abi.load()
@@ -49,10 +49,18 @@ class Solver:
         self._desc = _abi.make_desc(ncells, dxs, bc, c0, rho0, dt, _UINIT[uinit])
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        opts = None
+        if schedule is not None:
+            # schedule: per axis (variant, seqs_per_cta), None entries automatic
+            opts = _abi.PstdPlanOpts()
+            for i in range(3):
+                v, q = (schedule[i] if i < len(schedule) and schedule[i] else (None, None))
+                opts.variant[i] = -1 if v is None else int(v)
+                opts.seqs_per_cta[i] = -1 if q is None else int(q)
         h = ctypes.c_void_p()
-        rc = self.lib.pstd_plan(ctypes.byref(self._desc), ctypes.c_void_p(self.stream.cuda_stream),
-                                ctypes.byref(h))
-        _abi.check(self.lib, rc, "pstd_plan")
+        rc = self.lib.pstd_plan_ex(ctypes.byref(self._desc), ctypes.c_void_p(self.stream.cuda_stream),
+                                   ctypes.byref(opts) if opts is not None else None, ctypes.byref(h))
+        _abi.check(self.lib, rc, "pstd_plan_ex")
         self._h = h
         self.shapes = [self.field_shape(f) for f in range(self.ndim + 1)]
 
@@ -73,6 +81,15 @@ class Solver:
         sl = tuple(slice(*(lambda lo, hi: (lo, hi + 1))(*stored_node_range(n, b)))
                    for n, b in zip(self.ncells, self.bc))
         return p_full[sl]
+
+    def schedule(self):
+        """Per axis (variant, lanes per sequence, sequences per CTA, CTAs); -1s on the generic path."""
+        out = []
+        for a in range(self.ndim):
+            v = (ctypes.c_int * 4)()
+            _abi.check(self.lib, self.lib.pstd_plan_schedule(self._h, a, v), "pstd_plan_schedule")
+            out.append(tuple(v))
+        return out
 
     def last_launch_count(self) -> int:
         return int(self.lib.pstd_last_launch_count(self._h))
