@@ -168,6 +168,50 @@ int64_t pstd_last_launch_count(const pstd_plan_t* plan);
 /* Library version string. */
 const char* pstd_version(void);
 
+/* ---- Batched runs and reflection coefficients (Section 5) ------------------ */
+
+typedef struct pstd_batch_s pstd_batch_t;
+
+/* Plan `n` >= 1 independent simulations ("members"), member m described by
+ * descs[m] (sizes and walls may differ).  Each member gets a plan on its own
+ * stream; pstd_batch_run records one CUDA graph per block of steps in which
+ * every member is a parallel branch of `stream` (NULL: no graph, direct
+ * launches).  Errors: those of pstd_plan for any member. */
+int pstd_batch_plan(const pstd_desc* descs, int n, void* stream, pstd_batch_t** out);
+
+/* The plan of member i (for pstd_field_shape); owned by the batch. */
+int pstd_batch_member(const pstd_batch_t* batch, int i, pstd_plan_t** plan);
+
+/* pstd_init_velocity of every member.  p[m] is member m's pressure, and
+ * u[3 m + a] its velocity along axis a (device pointers).  Errors: PSTD_EINVAL. */
+int pstd_batch_init_velocity(pstd_batch_t* batch, float* const* p, float* const* u);
+
+/* `nsteps` leapfrog steps of every member, in place (pointers as above).
+ * Errors: PSTD_EINVAL, PSTD_ECUDA. */
+int pstd_batch_run(pstd_batch_t* batch, float* const* p, float* const* u, int64_t nsteps);
+
+/* out = sum_m w[m] p_m on the full node lattice x_j = j dx, j = 0..N_i per
+ * axis (shape (N_0+1, ..., N_{d-1}+1), C order), the weighted sum of
+ * Section 5.  All members must share ndim and ncells; a node a member does not
+ * store (a Dirichlet wall) contributes zero.  Sums in FP64, stores FP32.
+ * Valid as a reflection-coefficient field for t < 2 L / c0 (3 L / c0 when
+ * both walls of every axis are non-reflecting).  Errors: PSTD_EINVAL, PSTD_ECUDA. */
+int pstd_batch_combine(pstd_batch_t* batch, const double* w, float* const* p, float* out);
+
+/* Release the batch and its member plans (synchronises first). */
+int pstd_batch_free(pstd_batch_t* batch);
+
+/* Kernels launched by the last batch call (graph replays count their nodes). */
+int64_t pstd_batch_last_launch_count(const pstd_batch_t* batch);
+
+/* Section 5 on the host: for per-axis reflection coefficients
+ * refl[2 i] = R_L, refl[2 i + 1] = R_R, write the 4^ndim wall combinations as
+ * copies of *tmpl with bc replaced (axis 0 slowest; per axis in the order
+ * NN, ND, DN, DD) into descs[], and their weights, the product over axes of
+ * w = (1/4) M^T r with r = [R_L, 1, R_R, R_L R_R] and M the image-source
+ * polarity matrix, into w[].  Errors: PSTD_EINVAL. */
+int pstd_reflection_combos(const pstd_desc* tmpl, const double* refl, pstd_desc* descs, double* w);
+
 /* Capacity of pstd_step_noalloc: pressure points, and FFT length 2 N_i per axis. */
 #define PSTD_NOALLOC_MAX_POINTS (1 << 22)
 #define PSTD_NOALLOC_MAX_FFT 4096

@@ -32,6 +32,14 @@ SIGNATURES = {
     "pstd_dt_from_cfl": (c_double, [c_double, c_double, c_double]),
     "pstd_last_launch_count": (c_int64, [c_void_p]),
     "pstd_version": (c_char_p, []),
+    "pstd_batch_plan": (c_int, [c_void_p, c_int, c_void_p, POINTER(c_void_p)]),
+    "pstd_batch_member": (c_int, [c_void_p, c_int, POINTER(c_void_p)]),
+    "pstd_batch_init_velocity": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_void_p)]),
+    "pstd_batch_run": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_void_p), c_int64]),
+    "pstd_batch_combine": (c_int, [c_void_p, POINTER(c_double), POINTER(c_void_p), c_void_p]),
+    "pstd_batch_free": (c_int, [c_void_p]),
+    "pstd_batch_last_launch_count": (c_int64, [c_void_p]),
+    "pstd_reflection_combos": (c_int, [c_void_p, POINTER(c_double), c_void_p, POINTER(c_double)]),
     "pstd_step_noalloc": (c_int, [c_void_p, c_void_p, POINTER(c_void_p), c_int64, c_void_p]),
 }
 

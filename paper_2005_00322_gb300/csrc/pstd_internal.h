@@ -1,0 +1,17 @@
+// pstd_internal.h -- plan internals shared by the batch layer (not exported).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pstd.h"
+
+// Launch `n` leapfrog steps of plan P on its own stream (no graph capture of
+// its own, so the caller may be capturing); adds the kernel count.
+int pstd_internal_launch_steps(pstd_plan_t* P, float* p, float* const* u, int64_t n, int64_t* launches);
+// The plan's stream.
+cudaStream_t pstd_internal_stream(const pstd_plan_t* P);
+// First stored pressure node per axis (0 or 1) and the pressure shape.
+void pstd_internal_layout(const pstd_plan_t* P, int lo[3], int64_t shape[3]);
+// Record a CUDA error text for pstd_last_cuda_error().
+int pstd_internal_cuda_fail(cudaError_t e, const char* what);

@@ -24,6 +24,7 @@
 
 #include "../../include/pstd.h"
 #include "pstd_cta.cuh"
+#include "pstd_internal.h"
 #include "pstd_wkernels.cuh"
 
 namespace pstd {
@@ -330,17 +331,21 @@ int build_axis(pstd_plan_s* P, int i) {
     a.smem = pstd::cta_smem_bytes(G, a.L, a.rs);
     if (a.smem > 227 * 1024) return PSTD_EUNSUPPORTED;
 
-    // register-FFT passes where a schedule exists; an axis with too few line
-    // pairs to fill the GPU (4 per SM) takes the latency schedule
+    // register-FFT passes where a schedule exists.  Measured on GB300 (512^2
+    // and 256^3): the latency schedule (8 elements per lane) beats the
+    // throughput one wherever it exists, with 2 line pairs per CTA once the
+    // axis has enough lines to keep 2 CTAs per SM busy.
     int T = pstd::wlanes(a.L);
     int V = 0;
-    const int ov = P->opts.variant[i], os = P->opts.seqs_per_cta[i];
-    if (ov == 1 || (ov < 0 && pstd::wlanes_latency(a.L) > 0 && (a.nlines + 1) / 2 < 4 * 152)) {
+    int os = P->opts.seqs_per_cta[i];
+    const int ov = P->opts.variant[i];
+    if (ov == 1 || (ov < 0 && pstd::wlanes_latency(a.L) > 0)) {
         if (pstd::wlanes_latency(a.L) == 0) return PSTD_EINVAL;
         V = 1;
         T = pstd::wlanes_latency(a.L);
     }
     if (os == 0 || os > 256 || (os > 0 && (os & (os - 1)))) return PSTD_EINVAL;
+    if (os < 0 && V == 1 && T <= 128 && (a.nlines + 1) / 2 >= 2 * 2 * 152) os = 2;
     if (a.kind == 0 && T > 0) {
         std::vector<float2> wt;
         if (!wtw(a.L, V, wt)) return PSTD_EUNSUPPORTED;
@@ -506,6 +511,25 @@ int launch_grad(pstd_plan_s* P, int axis, int opi, const float* in, float* out, 
 }
 
 }  // namespace
+
+int pstd_internal_launch_steps(pstd_plan_t* P, float* p, float* const* u, int64_t n, int64_t* launches) {
+    for (int64_t s = 0; s < n; ++s) {
+        int rc = launch_step(P, p, u, launches);
+        if (rc != PSTD_OK) return rc;
+    }
+    return PSTD_OK;
+}
+
+cudaStream_t pstd_internal_stream(const pstd_plan_t* P) { return P->stream; }
+
+void pstd_internal_layout(const pstd_plan_t* P, int lo[3], int64_t shape[3]) {
+    for (int i = 0; i < 3; ++i) {
+        lo[i] = i < P->ndim ? P->ax[i].lo : 0;
+        shape[i] = P->shape[0][i];
+    }
+}
+
+int pstd_internal_cuda_fail(cudaError_t e, const char* what) { return cuda_fail(e, what); }
 
 extern "C" {
 

@@ -95,3 +95,18 @@ def test_static_helpers(lib):
 def test_library_is_built_for_sm103a():
     """The build passes exactly one -gencode for sm_103a."""
     assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_reflection_combos_match_oracle(lib):
+    """pstd_reflection_combos (host only) reproduces Section 5's weights."""
+    from oracle import reflection
+    from paper_2005_00322_gb300.batch import reflection_combos
+    for refl in [[(0.0, 0.0)], [(0.0, 0.5)], [(0.4, 0.4), (0.4, 0.4)], [(0.4, -0.2), (1.0, 0.0), (0.3, 0.3)]]:
+        bcs, w = reflection_combos((8,) * len(refl), 1e-4, refl)
+        ref = reflection.combination_weights(refl)
+        assert len(bcs) == len(ref)
+        for (b, wv), (rb, rw) in zip(zip(bcs, w), ref):
+            assert b == rb
+            assert abs(wv - rw) < 1e-15
+    _, w = reflection_combos((8,), 1e-4, [(0.0, 0.5)])
+    assert w == [0.375, 0.125, 0.375, 0.125]
