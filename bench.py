@@ -46,7 +46,18 @@ WORKLOADS = {
     "line256_dd": inputs.line256_dd,
     "cube256_ddnndd": lambda: inputs.cube256(steps=200),
     "cube384_dnd": lambda: inputs.cube384_dnd(),
+    # batched forms: leapfrog steps per bench step are reduced (the configured
+    # runs are 1500 / 4000 steps); --leapfrog-steps overrides
+    "cube256_r0.4": lambda: inputs.cube256_reflect(0.4, steps=32),
+    "plane_batch": lambda: inputs.plane_batch(steps=200),
 }
+
+
+def members_of(w):
+    """The independent runs of a workload: itself, its wall combinations or its batch."""
+    if isinstance(w, list):
+        return w
+    return [w]
 
 
 def cells(w) -> int:
@@ -172,6 +183,123 @@ def reference_arm(args, w, rank: int) -> None:
     print(json.dumps(line), flush=True)
 
 
+class SingleRunner:
+    """One grid through Solver (pstd_plan / pstd_run)."""
+
+    def __init__(self, w):
+        import torch
+        from paper_2005_00322_gb300 import Solver
+        self.w = w
+        self.solver = Solver(w.ncells, w.dx, w.bc, c0=w.c0, rho0=w.rho0, cfl=w.cfl)
+        self.stream = self.solver.stream
+        p0 = np.asarray(self.solver.restrict(w.p0_full()), np.float32)
+        self.p0 = torch.tensor(p0, device="cuda")
+        self.p, self.us = self.solver.zeros()
+        self.host_in = [torch.from_numpy(p0).pin_memory()] + \
+            [torch.zeros(sh, dtype=torch.float32).pin_memory() for sh in self.solver.shapes[1:]]
+        self.host_out = [torch.empty_like(h).pin_memory() for h in self.host_in]
+        self.cells = cells(w)
+        self.ndim = w.ndim
+        self.launches_per_step = w.ndim
+
+    def step(self):
+        self.p.copy_(self.p0)
+        for u in self.us:
+            u.zero_()
+        self.solver.init_velocity(self.p, self.us)
+        n = self.solver.last_launch_count()
+        self.solver.run(self.p, self.us, self.w.steps)
+        return n + self.solver.last_launch_count()
+
+    def step_e2e(self):
+        dev = [self.p] + self.us
+        for d, h in zip(dev, self.host_in):
+            d.copy_(h, non_blocking=True)
+        self.solver.init_velocity(self.p, self.us)
+        self.solver.run(self.p, self.us, self.w.steps)
+        for h, d in zip(self.host_out, dev):
+            h.copy_(d, non_blocking=True)
+
+    def leapfrog(self, n):
+        for _ in range(n):
+            self.solver.step(self.p, self.us)
+
+    def close(self):
+        self.solver.close()
+
+
+class BatchRunner:
+    """Independent grids in one batch (pstd_batch_*): wall combinations or a batch."""
+
+    def __init__(self, w):
+        import torch
+        from paper_2005_00322_gb300.batch import Batch, reflection_combos
+        self.w = w
+        if isinstance(w, list):
+            mem = w
+            specs = [dict(ncells=m.ncells, dx=m.dx, bc=m.bc, cfl=m.cfl, c0=m.c0, rho0=m.rho0) for m in mem]
+            p_full = [m.p0_full() for m in mem]
+            self.weights = None
+            self.steps = mem[0].steps
+        else:
+            bcs, self.weights = reflection_combos(w.ncells, w.dx, w.refl, w.c0, w.rho0, 1.0)
+            specs = [dict(ncells=w.ncells, dx=w.dx, bc=b, cfl=w.cfl, c0=w.c0, rho0=w.rho0) for b in bcs]
+            full = w.p0_full()
+            p_full = [full] * len(specs)
+            self.steps = w.steps
+        self.batch = Batch(specs)
+        self.stream = self.batch.stream
+        self.fields = self.batch.zeros()
+        self.p0 = []
+        self.host_in, self.host_out = [], []
+        for (p, us), spec, pf in zip(self.fields, specs, p_full):
+            sl = tuple(slice(1 if l == "D" else 0, (n - 1 if r == "D" else n) + 1)
+                       for n, (l, r) in zip(spec["ncells"], spec["bc"]))
+            q = np.ascontiguousarray(np.asarray(pf, np.float32)[sl])
+            self.p0.append(torch.tensor(q, device="cuda"))
+            hin = [torch.from_numpy(q).pin_memory()] + [torch.zeros(u.shape).pin_memory() for u in us]
+            self.host_in.append(hin)
+            self.host_out.append([torch.empty_like(h).pin_memory() for h in hin])
+        self.cells = sum(int(np.prod(sp["ncells"])) for sp in specs)
+        self.ndim = max(len(sp["ncells"]) for sp in specs)
+        self.launches_per_step = sum(len(sp["ncells"]) for sp in specs)
+        self.out = None
+        if self.weights is not None:
+            self.out = torch.empty(tuple(n + 1 for n in w.ncells), device="cuda")
+
+    def step(self):
+        for (p, us), q in zip(self.fields, self.p0):
+            p.copy_(q)
+            for u in us:
+                u.zero_()
+        self.batch.init_velocity(self.fields)
+        n = self.batch.last_launch_count()
+        self.batch.run(self.fields, self.steps)
+        n += self.batch.last_launch_count()
+        if self.weights is not None:
+            self.batch.combine(self.weights, self.fields, self.out)
+            n += self.batch.last_launch_count()
+        return n
+
+    def step_e2e(self):
+        for (p, us), hin in zip(self.fields, self.host_in):
+            for d, h in zip([p] + us, hin):
+                d.copy_(h, non_blocking=True)
+        self.batch.init_velocity(self.fields)
+        self.batch.run(self.fields, self.steps)
+        if self.weights is not None:
+            self.batch.combine(self.weights, self.fields, self.out)
+        for (p, us), hout in zip(self.fields, self.host_out):
+            for h, d in zip(hout, [p] + us):
+                h.copy_(d, non_blocking=True)
+
+    def leapfrog(self, n):
+        self.batch.run(self.fields, n)
+
+    def close(self):
+        self.batch.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -186,13 +314,17 @@ def main():
 
     w = WORKLOADS[args.workload]()
     if args.leapfrog_steps:
-        w.steps = args.leapfrog_steps
+        for m in members_of(w):
+            m.steps = args.leapfrog_steps
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    single = not isinstance(w, list) and w.refl is None
+    w0 = members_of(w)[0]
 
     if args.impl == "reference":
-        reference_arm(args, w, rank)
+        reference_arm(args, w0 if single or isinstance(w, list) else
+                      inputs.cube256(bc=(("N", "N"),) * 3, steps=w.steps), rank)
         return
 
     import torch
@@ -201,25 +333,14 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
-    from paper_2005_00322_gb300 import Solver
 
-    solver = Solver(w.ncells, w.dx, w.bc, c0=w.c0, rho0=w.rho0, cfl=w.cfl)
-    st = solver.stream
-    p0 = torch.tensor(np.asarray(solver.restrict(w.p0_full()), np.float32), device="cuda")
-    p, us = solver.zeros()
+    run = SingleRunner(w) if single else BatchRunner(w)
+    st = run.stream
+    steps_per = members_of(w)[0].steps
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
 
-    def one_step():
-        p.copy_(p0)
-        for u in us:
-            u.zero_()
-        solver.init_velocity(p, us)
-        n = solver.last_launch_count()
-        solver.run(p, us, w.steps)
-        return n + solver.last_launch_count()
-
     for _ in range(args.warmup):
-        one_step()
+        run.step()
     torch.cuda.synchronize()
 
     # device-resident timed region: CUDA events on the plan's stream per bench step
@@ -234,7 +355,7 @@ def main():
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(st)
-            launches += one_step()
+            launches += run.step()
             e1.record(st)
             e1.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
@@ -246,56 +367,52 @@ def main():
         tt = torch.tensor([t], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t = float(tt.item())
-    updates = cells(w) * w.steps * args.steps * world
+    updates = run.cells * steps_per * args.steps * world
     value = updates / t
 
-    # dominant kernel: the fused axis pass (k_step); average launch duration
-    # from events over direct launches of whole steps on the plan's stream
-    nk = 64
-    p.copy_(p0)
+    # dominant kernel: the fused axis pass; mean duration per launch from
+    # events around direct (non-graph) leapfrog steps on the plan's stream
+    nk = 64 if single else 4
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
-    for _ in range(nk):
-        solver.step(p, us)
+    run.leapfrog(nk)
     e1.record(st)
     e1.synchronize()
-    per_launch = e0.elapsed_time(e1) / 1e3 / (nk * w.ndim)
-    alg_bytes = 2 * (w.ndim + 1) * 4 * cells(w) / w.ndim     # per launch: one axis' share
+    step_s = e0.elapsed_time(e1) / 1e3 / nk
+    alg_step = sum(2 * (len(m) + 1) * 4 * int(np.prod(m)) for m in
+                   ([mm.ncells for mm in members_of(w)] if single or isinstance(w, list)
+                    else [w.ncells] * len(run.weights)))
+    if single:
+        per_launch = step_s / run.launches_per_step
+        alg_bytes = alg_step / run.launches_per_step
+    else:       # concurrent members: whole-step bandwidth
+        per_launch = step_s
+        alg_bytes = alg_step
     peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
     traffic = None
     if os.path.exists(TRAFFIC):
         tr = json.load(open(TRAFFIC))
-        ent = tr.get(w.name)
+        ent = tr.get(args.workload)
         if ent and ent.get("csrc_digest") == csrc_digest():
             traffic = ent.get("dram_bytes_per_launch")
     achieved = alg_bytes / per_launch / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "k_step",
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s",
-                "alg_bytes_per_launch": alg_bytes}
+                "frac": achieved / peak, "traffic": traffic, "kernel": "k_wstep (fused axis pass)",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
+                "alg_bytes_per_launch": alg_bytes,
+                "launch_s": per_launch if single else None, "step_s": step_s}
 
     # end to end through the public API with host buffers
-    ph = torch.from_numpy(np.asarray(solver.restrict(w.p0_full()), np.float32)).pin_memory()
-    uh = [torch.zeros(s, dtype=torch.float32).pin_memory() for s in solver.shapes[1:]]
-    po = torch.empty_like(ph).pin_memory()
-    uo = [torch.empty_like(u).pin_memory() for u in uh]
-    h2d = ph.numel() * 4 + sum(u.numel() * 4 for u in uh)
+    h2d = sum(h.numel() * 4 for h in (run.host_in if single else [x for m in run.host_in for x in m]))
     d2h = h2d
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        p.copy_(ph, non_blocking=True)
-        for u, h in zip(us, uh):
-            u.copy_(h, non_blocking=True)
-        solver.init_velocity(p, us)
-        solver.run(p, us, w.steps)
-        po.copy_(p, non_blocking=True)
-        for h, u in zip(uo, us):
-            h.copy_(u, non_blocking=True)
+        run.step_e2e()
         torch.cuda.synchronize()
     te = time.perf_counter() - t0
     if dist:
@@ -306,25 +423,31 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1:
-        n, el = oracle_sample(w, args.cpu_seconds)
-        cpu = {"value": cells(w) * n / el, "unit": UNIT, "cores": host_threads(), "kind": "oracle",
-               "sample": f"{n} FP64 leapfrog steps of the full {w.name} grid ({el:.1f} s)"}
+        wc = w0 if single or isinstance(w, list) else inputs.cube256(bc=(("N", "N"),) * 3)
+        n, el = oracle_sample(wc, args.cpu_seconds)
+        cpu = {"value": cells(wc) * n / el, "unit": UNIT, "cores": host_threads(), "kind": "oracle",
+               "sample": f"{n} FP64 leapfrog steps of the full {wc.name} grid ({el:.1f} s)"}
 
     if rank == 0:
+        nmem = 1 if single else (len(w) if isinstance(w, list) else len(run.weights))
+        cfg = {"workload": args.workload, "members": nmem,
+               "ncells": list(w0.ncells) if single or not isinstance(w, list) else "seeded, see inputs.plane_batch",
+               "cfl": w0.cfl, "leapfrog_steps_per_bench_step": steps_per,
+               "l2": "flushed (256 MB write) before each timed bench step",
+               "parallelism": "replicas" if world > 1 else "single GPU"}
+        if single:
+            cfg["bc"] = ["".join(b) for b in w.bc]
+        elif not isinstance(w, list):
+            cfg["reflection"] = w.refl
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w.name, "ncells": list(w.ncells),
-                       "bc": ["".join(b) for b in w.bc], "cfl": w.cfl,
-                       "leapfrog_steps_per_bench_step": w.steps,
-                       "l2": "flushed (256 MB write) before each timed bench step",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "config": cfg, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk.summary(), "gpu_launches": launches,
         }
         print(json.dumps(line), flush=True)
-    solver.close()
+    run.close()
     if dist:
         dist.destroy_process_group()
 

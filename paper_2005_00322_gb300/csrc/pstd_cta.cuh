@@ -119,7 +119,7 @@ PSTD_HD size_t cta_smem_bytes(int G, int L, int rs) {
 }
 
 PSTD_HD void cta_step(const StepArgs& a, int64_t block, void* smem, int tid, int nthr) {
-    const int L = a.opP.L;
+    const int L = a.opP.seqlen;
     const int nseq = (a.G + 1) / 2;
     float2* A = (float2*)smem;
     float2* B = A + (size_t)nseq * L;
@@ -162,7 +162,7 @@ PSTD_HD void cta_step(const StepArgs& a, int64_t block, void* smem, int tid, int
 }
 
 PSTD_HD void cta_grad(const GradArgs& a, int64_t block, void* smem, int tid, int nthr) {
-    const int L = a.op.L;
+    const int L = a.op.seqlen;
     const int nseq = (a.G + 1) / 2;
     float2* A = (float2*)smem;
     float2* B = A + (size_t)nseq * L;

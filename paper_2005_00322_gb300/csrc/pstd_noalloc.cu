@@ -203,6 +203,8 @@ extern "C" int pstd_step_noalloc(const pstd_desc* d, float* p, float* const* u, 
             op.f = tab + (size_t)(2 + dir) * kMaxFft;
             op.shift = tab + kMaxFft;
             op.dense = nullptr;
+            op.seqlen = L;
+            op.fold = 1.0f;
             op.fft = plans[i];
         }
         int64_t nl = 1, inner = 1;

@@ -46,8 +46,16 @@ struct FftPlan {
 };
 
 // One staggered derivative along one axis in one direction.
+//
+// kind 2 (convolution route, any N): the multiplier acting on the period-M
+// extension is a circular (group I) or skew-circular (group II) convolution
+// of length M = L with kernel h~[d] = sum_n f_n e^{2 pi i d n / L}
+// (times e^{i pi d / L} for group II).  It is evaluated as the linear
+// convolution of the extension with h~ through a power-of-two FFT of length
+// M2 >= 2L - 1 (table H = FFT_M2(h~) / M2), folded back as
+// y[pos] = y_lin[pos] + fold * y_lin[pos + L], fold = +1 (I) or -1 (II).
 struct LineOp {
-    int kind;               // 0: FFT route, 1: dense matrix route
+    int kind;               // 0: FFT route, 1: dense matrix route, 2: convolution route
     int N;                  // cells along the axis
     int L;                  // FFT length M = 2N
     int group2;             // 1: antiperiodic extension (ND, DN)
@@ -60,7 +68,9 @@ struct LineOp {
     const float2* f;        // L folded coefficients (complex)
     const float2* shift;    // group II: exp(-i pi j / L), j < L
     const float* dense;     // kind 1: nout x nin row-major operator
-    FftPlan fft;
+    int seqlen;             // buffer length of one sequence: L (kinds 0, 1) or M2 (kind 2)
+    float fold;             // kind 2: +1 (group I) or -1 (group II)
+    FftPlan fft;            // kinds 0 (length L) and 2 (length M2)
 };
 
 PSTD_HD float2 cmul(float2 a, float2 b) {
@@ -196,12 +206,16 @@ PSTD_HD void fft_pass(const FftPlan& P, int p, int& Ns, const float2* src, float
 // Build the extension of line pairs (2s, 2s+1) from raw into buf (FFT route).
 PSTD_HD void phase_extend(const LineOp& op, const float* raw, int rs, int G, float2* buf,
                           int tid, int nthr) {
-    const int L = op.L, N = op.N;
+    const int L = op.L, N = op.N, SL = op.seqlen;
     const int nseq = (G + 1) / 2;
-    const int total = nseq * L;
+    const int total = nseq * SL;
     for (int t = tid; t < total; t += nthr) {
-        const int s = t / L;
-        const int j = t - s * L;
+        const int s = t / SL;
+        const int j = t - s * SL;
+        if (j >= L) {   // kind 2: zero padding of the linear convolution
+            buf[(size_t)s * SL + j] = make_float2(0.0f, 0.0f);
+            continue;
+        }
         // position in the stored line and sign, or -1 for a zero
         int src;
         float sg;
@@ -225,17 +239,17 @@ PSTD_HD void phase_extend(const LineOp& op, const float* raw, int rs, int G, flo
             if (g1 < G) im = sg * raw[(size_t)g1 * rs + src];
         }
         float2 v = make_float2(re, im);
-        if (op.group2) v = cmul(v, PSTD_LDG(&op.shift[j]));
-        buf[(size_t)s * L + j] = v;
+        if (op.group2 && op.kind == 0) v = cmul(v, PSTD_LDG(&op.shift[j]));
+        buf[(size_t)s * SL + j] = v;
     }
 }
 
 // Multiply every sequence by the coefficient table.
 PSTD_HD void phase_multiply(const LineOp& op, float2* buf, int G, int tid, int nthr) {
-    const int L = op.L;
-    const int total = ((G + 1) / 2) * L;
+    const int SL = op.seqlen;
+    const int total = ((G + 1) / 2) * SL;
     for (int t = tid; t < total; t += nthr) {
-        const int n = t % L;
+        const int n = t % SL;
         buf[t] = cmul(buf[t], PSTD_LDG(&op.f[n]));
     }
 }
@@ -260,15 +274,17 @@ PSTD_HD void phase_dense(const LineOp& op, const float* raw, int rs, int G, floa
             a0 = fmaf(d, x0[j], a0);
             a1 = fmaf(d, x1[j], a1);
         }
-        buf[(size_t)s * op.L + base + i] = make_float2(a0, two ? a1 : 0.0f);
+        buf[(size_t)s * op.seqlen + base + i] = make_float2(a0, two ? a1 : 0.0f);
     }
 }
 
 // Output value of line g at stored output index i (after the inverse FFT).
 PSTD_HD float op_value(const LineOp& op, const float2* buf, int g, int i) {
     const int pos = op.dir == 0 ? i : i + op.out_lo;
-    float2 v = buf[(size_t)(g >> 1) * op.L + pos];
+    const float2* seq = buf + (size_t)(g >> 1) * op.seqlen;
+    float2 v = seq[pos];
     if (op.kind == 0 && op.group2) v = cmulc(v, PSTD_LDG(&op.shift[pos]));
+    if (op.kind == 2) v = cadd(v, cscale(seq[pos + op.L], op.fold));
     return (g & 1) ? v.y : v.x;
 }
 

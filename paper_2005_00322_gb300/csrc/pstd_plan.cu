@@ -60,7 +60,8 @@ namespace {
 
 thread_local std::string g_cuda_err;
 
-constexpr int kDenseMaxN = 256;
+constexpr int kDenseMaxN = 64;       // dense operator below this, convolution route above
+constexpr int kConvMaxFft = 8192;    // largest power-of-two FFT of the convolution route
 constexpr int kGraphSteps = 32;
 constexpr int kGraphCache = 4;
 constexpr size_t kSmemBudget = 100 * 1024;
@@ -68,7 +69,7 @@ constexpr size_t kSmemBudget = 100 * 1024;
 enum { OP_GRAD_P = 0, OP_GRAD_U = 1, OP_STEP_P = 2, OP_STEP_U = 3, OP_INIT_P = 4, OP_COUNT = 5 };
 
 struct Axis {
-    int N = 0, L = 0, group2 = 0, kind = 0;
+    int N = 0, L = 0, group2 = 0, kind = 0, M2 = 0;
     int lp = 0, lo = 0;               // stored pressure length, first stored node
     double dx = 0;
     int bcl = 0, bcr = 0;
@@ -249,6 +250,54 @@ std::vector<float> dense_operator(const Axis& a, int dir, double scale) {
     return D;
 }
 
+// In-place radix-2 FFT of a power-of-two length (FP64, host): forward
+// X_k = sum_j x_j e^{-2 pi i j k / n}.
+void host_fft(std::vector<std::complex<double>>& x) {
+    const size_t n = x.size();
+    for (size_t i = 1, j = 0; i < n; ++i) {
+        size_t bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(x[i], x[j]);
+    }
+    for (size_t len = 2; len <= n; len <<= 1) {
+        const double ang = -2.0 * M_PI / (double)len;
+        for (size_t i = 0; i < n; i += len)
+            for (size_t k = 0; k < len / 2; ++k) {
+                const std::complex<double> w(std::cos(ang * k), std::sin(ang * k));
+                const std::complex<double> u = x[i + k], v = x[i + k + len / 2] * w;
+                x[i + k] = u + v;
+                x[i + k + len / 2] = u - v;
+            }
+    }
+}
+
+// Convolution-route table of one direction at unit scale (see LineOp kind 2):
+// H = FFT_M2(h~) / M2 with h~[d] = sum_n f_n e^{2 pi i d n / L} (times
+// e^{i pi d / L} for group II), d < L, zero-padded to M2.
+std::vector<std::complex<double>> conv_table(const Axis& a, int dir) {
+    const int L = a.L;
+    std::vector<std::complex<double>> f(L), wl(L), h(a.M2, 0.0);
+    for (int n = 0; n < L; ++n) {
+        f[n] = coeff(a, n, dir, 1.0);
+        wl[n] = std::complex<double>(std::cos(2.0 * M_PI * n / L), std::sin(2.0 * M_PI * n / L));
+    }
+    for (int d = 0; d < L; ++d) {
+        std::complex<double> acc = 0;
+        int64_t idx = 0;
+        for (int n = 0; n < L; ++n) {
+            acc += f[n] * wl[idx];
+            idx += d;
+            if (idx >= L) idx -= L;
+        }
+        if (a.group2) acc *= std::complex<double>(std::cos(M_PI * d / L), std::sin(M_PI * d / L));
+        h[d] = acc;
+    }
+    host_fft(h);
+    for (auto& x : h) x /= (double)a.M2;
+    return h;
+}
+
 int build_axis(pstd_plan_s* P, int i) {
     Axis& a = P->ax[i];
     const pstd_desc& d = P->desc;
@@ -262,14 +311,22 @@ int build_axis(pstd_plan_s* P, int i) {
     const int hi = a.bcr == PSTD_DIRICHLET ? a.N - 1 : a.N;
     a.lp = hi - a.lo + 1;
     const bool fft_ok = radix_schedule(a.L, a.fft);
-    if (!fft_ok && a.N > kDenseMaxN) return PSTD_EUNSUPPORTED;
-    a.kind = fft_ok ? 0 : 1;
+    a.kind = fft_ok ? 0 : (a.N <= kDenseMaxN ? 1 : 2);
+    if (a.kind == 2) {
+        int M2 = 1;
+        while (M2 < 2 * a.L - 1) M2 *= 2;
+        if (M2 > kConvMaxFft || !radix_schedule(M2, a.fft)) return PSTD_EUNSUPPORTED;
+        a.M2 = M2;
+    }
 
     // twiddles and group-II shifts, FP64 -> FP32 once
-    std::vector<float2> tw(a.L), sh(a.L);
-    for (int m = 0; m < a.L; ++m) {
-        const double ang = 2.0 * M_PI * m / a.L;
+    const int FL = a.kind == 2 ? a.M2 : a.L;   // FFT length of the route
+    std::vector<float2> tw(FL), sh(a.L);
+    for (int m = 0; m < FL; ++m) {
+        const double ang = 2.0 * M_PI * m / FL;
         tw[m] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+    }
+    for (int m = 0; m < a.L; ++m) {
         const double ang2 = M_PI * m / a.L;
         sh[m] = make_float2((float)std::cos(ang2), (float)-std::sin(ang2));
     }
@@ -281,6 +338,11 @@ int build_axis(pstd_plan_s* P, int i) {
     const double scales[OP_COUNT] = {1.0, 1.0, -d.dt / d.rho0, -d.dt * d.rho0 * d.c0 * d.c0,
                                      d.dt / (2.0 * d.rho0)};
     const int dirs[OP_COUNT] = {0, 1, 0, 1, 0};
+    std::vector<std::complex<double>> conv[2];
+    if (a.kind == 2) {
+        conv[0] = conv_table(a, 0);
+        conv[1] = conv_table(a, 1);
+    }
     for (int o = 0; o < OP_COUNT; ++o) {
         const int dir = dirs[o];
         LineOp& op = a.op[o];
@@ -298,7 +360,17 @@ int build_axis(pstd_plan_s* P, int i) {
                               : (a.bcr == PSTD_NEUMANN ? -1.0f : 1.0f);
         op.shift = a.d_shift;
         op.fft = a.fft;
-        if (a.kind == 0) {
+        op.seqlen = FL;
+        op.fold = a.group2 ? -1.0f : 1.0f;
+        if (a.kind == 2) {
+            std::vector<float2> H(a.M2);
+            for (int n = 0; n < a.M2; ++n) {
+                const std::complex<double> c = conv[dir][n] * scales[o];
+                H[n] = make_float2((float)c.real(), (float)c.imag());
+            }
+            if ((rc = upload(H, &a.d_f[o])) != PSTD_OK) return rc;
+            op.f = a.d_f[o];
+        } else if (a.kind == 0) {
             std::vector<float2> f(a.L);
             for (int n = 0; n < a.L; ++n) {
                 std::complex<double> c = coeff(a, n, dir, scales[o]);
@@ -324,11 +396,11 @@ int build_axis(pstd_plan_s* P, int i) {
     a.inner = inner;
     a.rs = a.lp > a.N ? a.lp : a.N;
     int G = 16;
-    while (G > 2 && pstd::cta_smem_bytes(G, a.L, a.rs) > kSmemBudget) G -= 2;
+    while (G > 2 && pstd::cta_smem_bytes(G, FL, a.rs) > kSmemBudget) G -= 2;
     if ((int64_t)G > nl) G = (int)nl;
     if (G < 1) G = 1;
     a.G = G;
-    a.smem = pstd::cta_smem_bytes(G, a.L, a.rs);
+    a.smem = pstd::cta_smem_bytes(G, FL, a.rs);
     if (a.smem > 227 * 1024) return PSTD_EUNSUPPORTED;
 
     // register-FFT passes where a schedule exists.  Measured on GB300 (512^2

@@ -14,6 +14,10 @@ Workloads (sound speed 1500 m/s, density 1000 kg/m^3, dx = 0.1 mm):
   cube256_*       3-D, 256^3, one Gaussian blob (sigma 3 dx), CFL 0.3
   cube384_dnd     3-D, 384^3, Dirichlet x / Neumann y / Dirichlet z, 4 blobs,
                   CFL 0.3, 1000 steps
+  cube256_r0.4    3-D 256^3 with reflection coefficient 0.4 on every face:
+                  the 64 Neumann/Dirichlet combinations of Section 5
+  plane_batch     64 independent 2-D runs of seeded sizes in [64, 1024]^2
+                  with random walls (each wall N or D with probability 1/2)
 Blob centres are drawn uniformly in [4 sigma, L - 4 sigma] per axis so that the
 field is negligible at the walls.
 """
@@ -46,6 +50,7 @@ class Workload:
     dx: float = DX
     c0: float = C0
     rho0: float = RHO0
+    refl: list = None      # per axis (R_left, R_right) for reflection-coefficient runs
 
     @property
     def ndim(self) -> int:
@@ -112,6 +117,27 @@ def cube384_dnd(seed: int = 0) -> Workload:
     n = (384, 384, 384)
     return Workload("cube384_dnd", n, (("D", "D"), ("N", "N"), ("D", "D")), 0.3, 1000,
                     random_blobs(n, 4, 3.0, (0.5, 1.0), seed))
+
+
+def cube256_reflect(r: float = 0.4, seed: int = 0, steps: int = 1500) -> Workload:
+    """3-D 256^3, reflection coefficient r on all six faces (64 wall combinations)."""
+    w = cube256(seed=seed, steps=steps)
+    w.name = f"cube256_r{r:g}"
+    w.refl = [(r, r)] * 3
+    w.bc = (("N", "N"),) * 3     # placeholder: the 64 combinations replace it
+    return w
+
+
+def plane_batch(n: int = 64, seed: int = 0, steps: int = 4000, lo: int = 64, hi: int = 1024):
+    """n independent 2-D runs, sizes uniform in [lo, hi]^2, random walls, blobs, CFL 0.3."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for m in range(n):
+        ncells = (int(rng.integers(lo, hi + 1)), int(rng.integers(lo, hi + 1)))
+        bc = tuple(tuple("N" if rng.random() < 0.5 else "D" for _ in range(2)) for _ in range(2))
+        out.append(Workload(f"plane_batch[{m}]", ncells, bc, 0.3, steps,
+                            random_blobs(ncells, 4, 3.0, (0.5, 1.0), int(rng.integers(1 << 30)))))
+    return out
 
 
 def small(ncells, bc, cfl=0.3, steps=20, seed=0, nblobs=2, sigma_cells=2.0) -> Workload:

@@ -51,6 +51,9 @@ CASES = [
     ((16, 27, 25), [("N", "N"), ("D", "D"), ("N", "D")]),
     ((192, 20), [("D", "N"), ("N", "N")]), ((8, 96), [("N", "D"), ("D", "D")]),
     ((512, 6), [("N", "N"), ("D", "N")]), ((3, 384), [("D", "D"), ("N", "D")]),
+    # convolution route (2N has a prime factor > 5, N > 64): power-of-two linear convolution
+    ((67,), [("N", "N")]), ((97,), [("D", "N")]), ((257,), [("N", "D")]), ((130, 9), [("D", "D"), ("N", "N")]),
+    ((6, 101), [("N", "D"), ("D", "D")]),
     # dense route (2N has a factor 7, 11 or 13) and tiny edge sizes
     ((7,), [("N", "D")]), ((11,), [("D", "D")]), ((13, 6), [("N", "N"), ("D", "N")]),
     ((1,), [("N", "N")]), ((1,), [("N", "D")]), ((2,), [("D", "D")]), ((2, 3), [("D", "N"), ("N", "D")]),
@@ -182,6 +185,20 @@ def test_cube256_steps_and_modal():
     s.close()
 
 
+def test_large_prime_axis_run():
+    """N = 1021 (prime): convolution route with a 4096-point FFT, 200 steps vs the oracle."""
+    ncells, bcs = (1021,), [("D", "N")]
+    s, od = make(ncells, bcs, cfl=0.3)
+    w = inputs.small(ncells, bcs, nblobs=3, sigma_cells=6.0)
+    p0 = np.asarray(s.restrict(w.p0_full()), np.float32).astype(np.float64)
+    p, us = dev(p0), [torch.zeros(sh, device="cuda") for sh in s.shapes[1:]]
+    s.init_velocity(p, us)
+    s.run(p, us, 200)
+    ref = pstd.run(od, pstd.State(p0, pstd.init_velocity(od, p0, None, "halfstep")), 200)
+    assert rel_l2(host(p), ref.p) < 1e-4
+    s.close()
+
+
 def test_energy_drift_fp32():
     """The discrete energy of the GPU state stays constant over 1000 steps."""
     ncells, bcs = (60, 50), [("N", "D"), ("N", "N")]
@@ -206,7 +223,7 @@ def test_errors_surface():
     from paper_2005_00322_gb300 import Solver
     from paper_2005_00322_gb300._abi import PstdError
     with pytest.raises(PstdError, match="EUNSUPPORTED"):
-        Solver((257,), DX, [("N", "N")], cfl=0.2)      # 2N = 514 = 2 * 257, N > 256
+        Solver((4099,), DX, [("N", "N")], cfl=0.2)     # prime N: convolution FFT beyond 8192
     with pytest.raises(PstdError, match="EUNSTABLE"):
         Solver((64,), DX, [("N", "N")], cfl=0.7)
     s, _ = make((16,), [("N", "N")])
