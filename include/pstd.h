@@ -102,6 +102,12 @@ int pstd_plan(const pstd_desc* desc, void* stream, pstd_plan_t** out);
 typedef struct {
     int variant[3];
     int seqs_per_cta[3];
+    /* 0: spectral derivatives through FFTs of the symmetric extension (default);
+     * 1: split-precision dense form -- each derivative as a GEMM with the
+     *    FP64-built operator matrix, FP16 hi/lo split products on the tensor
+     *    cores with FP32 accumulation (axes with N <= 1024); affects
+     *    pstd_step / pstd_run only. */
+    int form;
 } pstd_plan_opts;
 
 /* pstd_plan with explicit schedule options (NULL = all automatic).

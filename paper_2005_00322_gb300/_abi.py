@@ -60,7 +60,7 @@ class PstdDesc(ctypes.Structure):
 
 class PstdPlanOpts(ctypes.Structure):
     """Mirror of pstd_plan_opts (-1 = automatic)."""
-    _fields_ = [("variant", c_int * 3), ("seqs_per_cta", c_int * 3)]
+    _fields_ = [("variant", c_int * 3), ("seqs_per_cta", c_int * 3), ("form", c_int)]
 
 
 class PstdError(RuntimeError):

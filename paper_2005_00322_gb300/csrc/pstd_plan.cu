@@ -24,7 +24,9 @@
 
 #include "../../include/pstd.h"
 #include "pstd_cta.cuh"
+#include "pstd_gemm.h"
 #include "pstd_internal.h"
+#include <cuda_fp16.h>
 #include "pstd_wkernels.cuh"
 
 namespace pstd {
@@ -88,6 +90,11 @@ struct Axis {
     float2* d_wtw = nullptr;
     WAxis wax{};
     WLaunch wgeo{};
+    // split-precision dense form
+    uint4* d_gemm = nullptr;          // A1h | A1l | A2h | A2l fragments
+    pstd::GemmAxis gax{};
+    unsigned ggrid = 0;
+    size_t gsmem = 0;
 };
 
 // register-FFT dispatch by length and schedule variant
@@ -161,7 +168,7 @@ bool radix_schedule(int L, FftPlan& P) {
 
 struct pstd_plan_s {
     pstd_desc desc{};
-    pstd_plan_opts opts{{-1, -1, -1}, {-1, -1, -1}};
+    pstd_plan_opts opts{{-1, -1, -1}, {-1, -1, -1}, 0};
     cudaStream_t stream = nullptr;
     int ndim = 0;
     int64_t shape[4][3] = {};
@@ -204,7 +211,7 @@ int upload(const std::vector<T>& h, T** d) {
 
 // Dense operator (rows: stored outputs, cols: stored inputs) of the same
 // multiplier, FP64, for axes with no FFT schedule.
-std::vector<float> dense_operator(const Axis& a, int dir, double scale) {
+std::vector<double> dense_operator64(const Axis& a, int dir, double scale) {
     const int N = a.N, L = a.L;
     std::vector<std::complex<double>> K(L);
     for (int d = 0; d < L; ++d) {
@@ -219,7 +226,7 @@ std::vector<float> dense_operator(const Axis& a, int dir, double scale) {
     const int nout = dir == 0 ? N : a.lp;
     const double sR = dir == 0 ? (a.bcr == PSTD_NEUMANN ? 1.0 : -1.0)
                                : (a.bcr == PSTD_NEUMANN ? -1.0 : 1.0);
-    std::vector<float> D((size_t)nout * nin);
+    std::vector<double> D((size_t)nout * nin);
     for (int i = 0; i < nout; ++i) {
         const int pos = dir == 0 ? i : i + a.lo;
         for (int j = 0; j < nin; ++j) {
@@ -244,10 +251,55 @@ std::vector<float> dense_operator(const Axis& a, int dir, double scale) {
                 }
                 v += sg[m] * k.real();
             }
-            D[(size_t)i * nin + j] = (float)v;
+            D[(size_t)i * nin + j] = v;
         }
     }
     return D;
+}
+
+std::vector<float> dense_operator(const Axis& a, int dir, double scale) {
+    std::vector<double> d = dense_operator64(a, dir, scale);
+    return std::vector<float>(d.begin(), d.end());
+}
+
+// Fragment-ordered FP16 hi / lo copies of D / max|D| (rows m < M, cols k < K)
+// for mma m16n8k16: per (16-row tile, 16-column tile) 32 lanes x 4 words.
+// The low part is stored multiplied by 2^11 (see pstd_gemm.cu).
+void gemm_fragments(const std::vector<double>& D, int M, int K, std::vector<uint4>& hi,
+                    std::vector<uint4>& lo, double& scale) {
+    double mx = 0;
+    for (double v : D) mx = std::fabs(v) > mx ? std::fabs(v) : mx;
+    scale = mx > 0 ? mx : 1.0;
+    const int MT = (M + 15) / 16, KT = (K + 15) / 16;
+    hi.assign((size_t)MT * KT * 32, uint4{0, 0, 0, 0});
+    lo.assign(hi.size(), uint4{0, 0, 0, 0});
+    auto el = [&](int m, int k, bool low) -> uint16_t {
+        double x = (m < M && k < K) ? D[(size_t)m * K + k] / scale : 0.0;
+        const __half h = __float2half_rn((float)x);
+        __half r = h;
+        if (low) r = __float2half_rn((float)((x - (double)__half2float(h)) * 2048.0));
+        uint16_t bits;
+        std::memcpy(&bits, &r, 2);
+        return bits;
+    };
+    auto pack = [&](int m, int k, bool low) -> unsigned {
+        return (unsigned)el(m, k, low) | ((unsigned)el(m, k + 1, low) << 16);
+    };
+    for (int mt = 0; mt < MT; ++mt)
+        for (int kt = 0; kt < KT; ++kt)
+            for (int lane = 0; lane < 32; ++lane) {
+                const int g = lane >> 2, t = lane & 3;
+                const int m0 = mt * 16 + g, k0 = kt * 16 + 2 * t;
+                for (int part = 0; part < 2; ++part) {
+                    const bool low = part == 1;
+                    uint4 r;
+                    r.x = pack(m0, k0, low);
+                    r.y = pack(m0 + 8, k0, low);
+                    r.z = pack(m0, k0 + 8, low);
+                    r.w = pack(m0 + 8, k0 + 8, low);
+                    (low ? lo : hi)[((size_t)mt * KT + kt) * 32 + lane] = r;
+                }
+            }
 }
 
 // In-place radix-2 FFT of a power-of-two length (FP64, host): forward
@@ -468,6 +520,48 @@ int build_axis(pstd_plan_s* P, int i) {
         a.wl = T;
         a.wv = V;
     }
+
+    // split-precision dense form
+    if (P->opts.form == 1) {
+        if (a.N > 1024) return PSTD_EUNSUPPORTED;
+        std::vector<uint4> h1, l1, h2, l2;
+        double s1, s2;
+        gemm_fragments(dense_operator64(a, 0, scales[OP_STEP_P]), a.N, a.lp, h1, l1, s1);
+        gemm_fragments(dense_operator64(a, 1, scales[OP_STEP_U]), a.lp, a.N, h2, l2, s2);
+        std::vector<uint4> all;
+        all.insert(all.end(), h1.begin(), h1.end());
+        all.insert(all.end(), l1.begin(), l1.end());
+        all.insert(all.end(), h2.begin(), h2.end());
+        all.insert(all.end(), l2.begin(), l2.end());
+        if ((rc = upload(all, &a.d_gemm)) != PSTD_OK) return rc;
+        pstd::GemmAxis& g = a.gax;
+        g.N = a.N;
+        g.lp = a.lp;
+        g.MT1 = (a.N + 15) / 16;
+        g.KT1 = (a.lp + 15) / 16;
+        g.MT2 = (a.lp + 15) / 16;
+        g.KT2 = (a.N + 15) / 16;
+        g.A1h = a.d_gemm;
+        g.A1l = g.A1h + h1.size();
+        g.A2h = g.A1l + l1.size();
+        g.A2l = g.A2h + h2.size();
+        g.s1 = (float)s1;
+        g.s2 = (float)s2;
+        g.nlines = a.nlines;
+        g.inner = a.inner;
+        // lines per CTA: fit shared memory, and shrink until the axis has at
+        // least one CTA per SM
+        int G = 64;
+        while (G > 8 && pstd::gemm_smem_bytes(G, g.KT1, g.KT2, a.N) > 200 * 1024) G /= 2;
+        auto ctas = [&](int gg) {
+            return a.inner == 1 ? (a.nlines + gg - 1) / gg : (a.nlines / a.inner) * ((a.inner + gg - 1) / gg);
+        };
+        while (G > 8 && ctas(G) < 152) G /= 2;
+        g.G = G;
+        a.gsmem = pstd::gemm_smem_bytes(G, g.KT1, g.KT2, a.N);
+        if (a.inner == 1) a.ggrid = (unsigned)((a.nlines + G - 1) / G);
+        else a.ggrid = (unsigned)((a.nlines / a.inner) * ((a.inner + G - 1) / G));
+    }
     return PSTD_OK;
 }
 
@@ -476,6 +570,7 @@ void free_plan_memory(pstd_plan_s* P) {
         cudaFree(a.d_tw);
         cudaFree(a.d_shift);
         cudaFree(a.d_wtw);
+        cudaFree(a.d_gemm);
         for (int o = 0; o < OP_COUNT; ++o) {
             cudaFree(a.d_f[o]);
             cudaFree(a.d_dense[o]);
@@ -534,6 +629,17 @@ StepArgs step_args(pstd_plan_s* P, int a, float* p, float* const* u) {
 int launch_step(pstd_plan_s* P, float* p, float* const* u, int64_t* launches) {
     for (int a = P->ndim - 1; a >= 0; --a) {
         Axis& A = P->ax[a];
+        if (P->opts.form == 1) {
+            pstd::GemmStep g;
+            g.ax = A.gax;
+            g.p = p;
+            g.u = u[a];
+            g.acc_in = (a == P->ndim - 1) ? p : P->d_S;
+            g.acc_out = (a == 0) ? p : P->d_S;
+            CK(pstd::launch_gemm_step(A.ggrid, A.gsmem, P->stream, g));
+            ++*launches;
+            continue;
+        }
         if (A.wl) {
             WStep w;
             w.ax = A.wax;
@@ -651,6 +757,10 @@ int pstd_plan_ex(const pstd_desc* desc, void* stream, const pstd_plan_opts* opts
     if (!P) return PSTD_ENOMEM;
     P->desc = *desc;
     if (opts) P->opts = *opts;
+    if (P->opts.form != 0 && P->opts.form != 1) {
+        delete P;
+        return PSTD_EINVAL;
+    }
     P->stream = (cudaStream_t)stream;
     P->ndim = desc->ndim;
     for (int f = 0; f < 4; ++f)
@@ -675,6 +785,13 @@ int pstd_plan_ex(const pstd_desc* desc, void* stream, const pstd_plan_opts* opts
         for (int i = 0; i < P->ndim; ++i) mx = P->ax[i].smem > mx ? P->ax[i].smem : mx;
         cudaError_t e = pstd::set_max_smem((int)mx);
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaFuncSetAttribute");
+        if (rc == PSTD_OK && P->opts.form == 1) {
+            int dev = 0, optin = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            e = pstd::gemm_set_smem(optin);
+            if (e != cudaSuccess) rc = cuda_fail(e, "cudaFuncSetAttribute(split-precision pass)");
+        }
         for (int i = 0; i < P->ndim && rc == PSTD_OK; ++i) {
             if (!P->ax[i].wl) continue;
             int dev = 0, optin = 0;

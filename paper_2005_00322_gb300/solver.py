@@ -32,7 +32,7 @@ class Solver:
     """
 
     def __init__(self, ncells, dx, bc, c0=1500.0, rho0=1000.0, dt=None, cfl=None,
-                 uinit="halfstep", device=None, stream=None, schedule=None):
+                 uinit="halfstep", device=None, stream=None, schedule=None, form="fft"):
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the PSTD library runs on the GPU only")
         self.lib = _abi.load()
@@ -50,13 +50,16 @@ class Solver:
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
         opts = None
-        if schedule is not None:
+        if form not in ("fft", "split"):
+            raise ValueError("form is 'fft' or 'split'")
+        if schedule is not None or form != "fft":
             # schedule: per axis (variant, seqs_per_cta), None entries automatic
             opts = _abi.PstdPlanOpts()
             for i in range(3):
-                v, q = (schedule[i] if i < len(schedule) and schedule[i] else (None, None))
+                v, q = (schedule[i] if schedule and i < len(schedule) and schedule[i] else (None, None))
                 opts.variant[i] = -1 if v is None else int(v)
                 opts.seqs_per_cta[i] = -1 if q is None else int(q)
+            opts.form = 1 if form == "split" else 0
         h = ctypes.c_void_p()
         rc = self.lib.pstd_plan_ex(ctypes.byref(self._desc), ctypes.c_void_p(self.stream.cuda_stream),
                                    ctypes.byref(opts) if opts is not None else None, ctypes.byref(h))
