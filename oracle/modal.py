@@ -31,7 +31,12 @@ from .pstd import TABLE2, Desc, p_nodes
 
 
 def mode_wavenumbers(n: int, bc: tuple, dx: float) -> np.ndarray:
-    """Wavenumber of each T1 output entry of one axis (Table 1, M = 2N)."""
+    """Wavenumber of each T1 output entry of one axis (Table 1, M = 2N).
+
+    A periodic axis uses the DFT and the wavenumbers of Section 2."""
+    if bc == ("P", "P"):
+        from .pstd import fourier_wavenumbers
+        return fourier_wavenumbers(n, dx)
     L = n * dx
     T1 = TABLE2[bc][0]
     if T1 == "C1":      # n = 0..N
@@ -54,11 +59,31 @@ def _omega_dt(desc: Desc) -> np.ndarray:
     return 2.0 * np.arcsin(s)
 
 
+def _forward(bc, P, axis):
+    if bc == ("P", "P"):
+        from .pstd import dft_matrix
+        n = P.shape[axis]
+        return np.moveaxis(np.moveaxis(P, axis, -1) @ dft_matrix(n).T, -1, axis)
+    if np.iscomplexobj(P):      # a periodic axis was transformed already
+        return dtt.apply(TABLE2[bc][0], P.real, axis) + 1j * dtt.apply(TABLE2[bc][0], P.imag, axis)
+    return dtt.apply(TABLE2[bc][0], P, axis)
+
+
+def _inverse(bc, P, axis):
+    if bc == ("P", "P"):
+        from .pstd import dft_matrix
+        n = P.shape[axis]
+        return np.moveaxis((np.moveaxis(P, axis, -1) @ np.conj(dft_matrix(n)).T) / n, -1, axis)
+    if np.iscomplexobj(P):
+        return dtt.inverse(TABLE2[bc][0], P.real, axis) + 1j * dtt.inverse(TABLE2[bc][0], P.imag, axis)
+    return dtt.inverse(TABLE2[bc][0], P, axis)
+
+
 def modal_pressure(desc: Desc, p0: np.ndarray, nsteps: int, uinit: str = "halfstep") -> np.ndarray:
     """p after ``nsteps`` leapfrog steps from p0 with zero initial velocity."""
     P = np.asarray(p0, dtype=np.float64)
     for i in range(desc.ndim):
-        P = dtt.apply(TABLE2[desc.bc[i]][0], P, i)
+        P = _forward(desc.bc[i], P, i)
     wdt = _omega_dt(desc)
     if uinit == "halfstep":
         P = P * np.cos(nsteps * wdt)
@@ -67,8 +92,8 @@ def modal_pressure(desc: Desc, p0: np.ndarray, nsteps: int, uinit: str = "halfst
     else:
         raise ValueError(uinit)
     for i in range(desc.ndim):
-        P = dtt.inverse(TABLE2[desc.bc[i]][0], P, i)
-    return P
+        P = _inverse(desc.bc[i], P, i)
+    return P.real if np.iscomplexobj(P) else P
 
 
 def separable_modal_pressure(desc: Desc, factors: list, nsteps: int,
@@ -107,6 +132,8 @@ def node_weights(n: int, bc: tuple) -> np.ndarray:
     """Quadrature weight of each stored pressure node: 1/2 on a Neumann wall node."""
     j = p_nodes(n, bc)
     w = np.ones(len(j))
+    if bc == ("P", "P"):
+        return w
     if bc[0] == "N":
         w[0] = 0.5
     if bc[1] == "N":

@@ -46,6 +46,7 @@ from . import dtt
 
 NEUMANN = "N"
 DIRICHLET = "D"
+PERIODIC = "P"      # Table 2's periodic row: the Fourier PSTD method of Section 2
 
 # Table 2: (left, right) -> (T1, T2, sign of a1, sign of a2)
 TABLE2 = {
@@ -79,7 +80,11 @@ class Desc:
 
 
 def p_nodes(n: int, bc: tuple) -> np.ndarray:
-    """Indices j of the stored pressure nodes x_j = j dx (Dirichlet walls dropped)."""
+    """Indices j of the stored pressure nodes x_j = j dx (Dirichlet walls dropped).
+
+    A periodic axis stores the N nodes j = 0..N-1 (node N is node 0)."""
+    if bc == (PERIODIC, PERIODIC):
+        return np.arange(0, n)
     lo = 1 if bc[0] == DIRICHLET else 0
     hi = n - 1 if bc[1] == DIRICHLET else n
     return np.arange(lo, hi + 1)
@@ -110,8 +115,37 @@ def wavenumbers(n: int, bc: tuple, dx: float):
     return 2.0 * np.pi * (np.arange(0, n) + 0.5) / (M * dx)
 
 
+def fourier_wavenumbers(n: int, dx: float) -> np.ndarray:
+    """k_n = 2 pi n / (N dx) in DFT order, n in [-N/2, N/2 - 1] (even N) or
+    [-(N-1)/2, (N-1)/2] (odd N), Section 2."""
+    idx = np.arange(n)
+    nn = np.where(idx < (n + 1) // 2, idx, idx - n)
+    if n % 2 == 0:
+        nn[n // 2] = -n // 2
+    return 2.0 * np.pi * nn / (n * dx)
+
+
+def dft_matrix(n: int) -> np.ndarray:
+    """F[k, j] = exp(-2 pi i j k / N), the discrete Fourier transform."""
+    j = np.arange(n)
+    return np.exp(-2j * np.pi * np.outer(j, j) / n)
+
+
+def fourier_grad(x: np.ndarray, axis: int, n: int, dx: float, shift: float) -> np.ndarray:
+    """F^{-1}{ i k e^{i k shift} F{x} } along ``axis`` (Eq. fourier_pstd_solution)."""
+    k = fourier_wavenumbers(n, dx)
+    F = dft_matrix(n)
+    xm = np.moveaxis(np.asarray(x, np.float64), axis, -1)
+    X = xm @ F.T
+    Y = X * (1j * k * np.exp(1j * k * shift))
+    y = (Y @ np.conj(F).T) / n
+    return np.moveaxis(y.real, -1, axis)
+
+
 def grad_p(p: np.ndarray, axis: int, n: int, bc: tuple, dx: float) -> np.ndarray:
     """T2^{-1}{ a1 T1{p} } along ``axis``: pressure nodes -> velocity half-nodes."""
+    if bc == (PERIODIC, PERIODIC):
+        return fourier_grad(p, axis, n, dx, +0.5 * dx)
     T1, T2, s1, _ = TABLE2[bc]
     M = 2 * n
     k = wavenumbers(n, bc, dx)
@@ -134,6 +168,8 @@ def grad_p(p: np.ndarray, axis: int, n: int, bc: tuple, dx: float) -> np.ndarray
 
 def grad_u(u: np.ndarray, axis: int, n: int, bc: tuple, dx: float) -> np.ndarray:
     """T1^{-1}{ a2 T2{u} } along ``axis``: velocity half-nodes -> pressure nodes."""
+    if bc == (PERIODIC, PERIODIC):
+        return fourier_grad(u, axis, n, dx, -0.5 * dx)
     T1, T2, _, s2 = TABLE2[bc]
     M = 2 * n
     k = wavenumbers(n, bc, dx)

@@ -295,3 +295,64 @@ def test_planted_index_shift_is_caught(monkeypatch):
     monkeypatch.setattr(pstd, "grad_p", shifted)
     s = pstd.run(d, pstd.State(p0, pstd.init_velocity(d, p0, None, "halfstep")), 20)
     assert np.abs(s.p - ref).max() > 1e-3
+
+
+# ---- periodic Fourier PSTD (Section 2; Table 2's periodic row) -----------------
+
+@pytest.mark.parametrize("n", [8, 9, 16, 31])
+def test_fourier_single_modes(n):
+    """i k e^{+-i k dx/2} differentiates each resolved Fourier mode exactly onto the
+    staggered grid; the even-N Nyquist mode maps to a real multiple of itself."""
+    dx = 0.23
+    x = np.arange(n) * dx
+    xm = x + 0.5 * dx
+    for m in range(1, (n - 1) // 2 + 1):
+        k = 2 * np.pi * m / (n * dx)
+        for ph in (0.0, 0.7):
+            p = np.cos(k * x + ph)
+            assert np.abs(pstd.grad_p(p, 0, n, ("P", "P"), dx) + k * np.sin(k * xm + ph)).max() < 1e-11 * k * n
+            u = np.sin(k * xm + ph)
+            assert np.abs(pstd.grad_u(u, 0, n, ("P", "P"), dx) - k * np.cos(k * x + ph)).max() < 1e-11 * k * n
+    if n % 2 == 0:
+        kn = np.pi / dx
+        p = np.cos(kn * x)                    # (-1)^j
+        assert np.abs(pstd.grad_p(p, 0, n, ("P", "P"), dx) + kn * np.sin(kn * xm)).max() < 1e-10 * kn
+
+
+def test_fourier_modal_and_energy():
+    """Periodic 2-D: modal closed form vs stepping; energy conserved."""
+    d = _desc((12, 9), [("P", "P"), ("D", "N")], cfl=0.2)
+    p0 = np.random.default_rng(4).standard_normal(pstd.field_shapes(d)[0])
+    s = pstd.run(d, pstd.State(p0, pstd.init_velocity(d, p0, None, "halfstep")), 200)
+    assert np.abs(s.p - modal.modal_pressure(d, p0, 200)).max() < 1e-11 * np.abs(p0).max()
+    s = pstd.State(p0, pstd.init_velocity(d, p0, None, "halfstep"))
+    es = []
+    for _ in range(30):
+        s1 = pstd.step(d, s)
+        es.append(modal.energy(d, s.p, s.u, s1.u))
+        s = s1
+    assert np.abs(np.array(es) - es[0]).max() < 1e-12 * es[0]
+
+
+def test_fourier_wave_wraps_around():
+    """Fig. 1: a right-going pulse leaves through one side and re-enters through the
+    other; after t = L / c0 it is back where it started (periodic images)."""
+    n, cfl, sig = 128, 0.05, 4.0
+    d = _desc((n,), [("P", "P")], cfl=cfl)
+    dx = d.dx[0]
+    x = np.arange(n) * dx
+    L = n * dx
+
+    def g(z):
+        z = (z + L / 2) % L - L / 2          # nearest periodic image
+        return np.exp(-(z ** 2) / (2 * (sig * dx) ** 2))
+    x0 = 40 * dx
+    p0 = g(x - x0)
+    u0 = [g(x + 0.5 * dx - x0) / (1000.0 * 1500.0)]   # right-going: u = p / (rho0 c0)
+    steps = int(round(n / cfl))
+    s = pstd.run(d, pstd.State(p0, pstd.init_velocity(d, p0, u0, "halfstep")), steps)
+    ct = 1500.0 * steps * d.dt
+    assert abs(ct - L) < 1e-12
+    assert np.abs(s.p - p0).max() < 2e-3
+    half = pstd.run(d, pstd.State(p0, pstd.init_velocity(d, p0, u0, "halfstep")), steps // 2)
+    assert np.abs(half.p - g(x - x0 - L / 2)).max() < 2e-3
