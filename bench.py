@@ -252,9 +252,10 @@ class BatchRunner:
         self.fields = self.batch.zeros()
         self.p0 = []
         self.host_in, self.host_out = [], []
+        from paper_2005_00322_gb300.solver import stored_node_range
         for (p, us), spec, pf in zip(self.fields, specs, p_full):
-            sl = tuple(slice(1 if l == "D" else 0, (n - 1 if r == "D" else n) + 1)
-                       for n, (l, r) in zip(spec["ncells"], spec["bc"]))
+            sl = tuple(slice(stored_node_range(n, b)[0], stored_node_range(n, b)[1] + 1)
+                       for n, b in zip(spec["ncells"], spec["bc"]))
             q = np.ascontiguousarray(np.asarray(pf, np.float32)[sl])
             self.p0.append(torch.tensor(q, device="cuda"))
             hin = [torch.from_numpy(q).pin_memory()] + [torch.zeros(u.shape).pin_memory() for u in us]

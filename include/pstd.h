@@ -45,8 +45,12 @@ extern "C" {
 #endif
 
 /* Wall type.  Table 2: Neumann <-> whole-sample symmetric pressure,
- * Dirichlet <-> whole-sample antisymmetric pressure. */
-typedef enum { PSTD_NEUMANN = 0, PSTD_DIRICHLET = 1 } pstd_bc;
+ * Dirichlet <-> whole-sample antisymmetric pressure.  PSTD_PERIODIC (both
+ * walls of an axis) is Table 2's periodic row, the Fourier PSTD method of
+ * Section 2 (Eq. fourier_pstd_solution): the axis stores the N nodes
+ * j = 0..N-1 and its derivatives are i k e^{+-i k dx/2} with the DFT
+ * wavenumbers of Section 2. */
+typedef enum { PSTD_NEUMANN = 0, PSTD_DIRICHLET = 1, PSTD_PERIODIC = 2 } pstd_bc;
 
 /* How pstd_init_velocity derives u^{-1/2} from the given u(0).
  * PSTD_U_HALFSTEP: u^{-1/2} = u0 + (dt / (2 rho0)) D_p p^0, so that the

@@ -8,7 +8,7 @@ from ctypes import POINTER, c_char_p, c_double, c_int, c_int64, c_void_p
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libpstd.so")
 
-NEUMANN, DIRICHLET = 0, 1
+NEUMANN, DIRICHLET, PERIODIC = 0, 1, 2
 U_HALFSTEP, U_AS_GIVEN = 0, 1
 
 ERRORS = {0: "PSTD_OK", -1: "PSTD_EINVAL", -2: "PSTD_EUNSTABLE", -3: "PSTD_ENOMEM",
@@ -114,7 +114,7 @@ def make_desc(ncells, dx, bc, c0, rho0, dt, uinit=U_HALFSTEP) -> PstdDesc:
         for s in range(2):
             if i < d.ndim:
                 b = bc[i][s]
-                d.bc[i][s] = {"N": NEUMANN, "D": DIRICHLET}.get(b, b) if isinstance(b, str) else int(b)
+                d.bc[i][s] = {"N": NEUMANN, "D": DIRICHLET, "P": PERIODIC}.get(b, b) if isinstance(b, str) else int(b)
             else:
                 d.bc[i][s] = NEUMANN
     d.c0, d.rho0, d.dt, d.uinit = float(c0), float(rho0), float(dt), int(uinit)

@@ -174,10 +174,11 @@ class ReflectionRun:
 
     def set_initial_pressure(self, p_full):
         """p0 on the full node lattice (N_i + 1 per axis); velocities start at zero."""
+        from .solver import stored_node_range
         p_full = torch.as_tensor(p_full, dtype=torch.float32, device=self.batch.device)
         for (p, us), bc in zip(self.fields, self.bcs):
-            sl = tuple(slice(1 if l == "D" else 0, (n - 1 if r == "D" else n) + 1)
-                       for n, (l, r) in zip(self.ncells, bc))
+            sl = tuple(slice(stored_node_range(n, b)[0], stored_node_range(n, b)[1] + 1)
+                       for n, b in zip(self.ncells, bc))
             p.copy_(p_full[sl])
             for u in us:
                 u.zero_()

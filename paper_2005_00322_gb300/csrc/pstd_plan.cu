@@ -71,7 +71,7 @@ constexpr size_t kSmemBudget = 100 * 1024;
 enum { OP_GRAD_P = 0, OP_GRAD_U = 1, OP_STEP_P = 2, OP_STEP_U = 3, OP_INIT_P = 4, OP_COUNT = 5 };
 
 struct Axis {
-    int N = 0, L = 0, group2 = 0, kind = 0, M2 = 0;
+    int N = 0, L = 0, group2 = 0, kind = 0, M2 = 0, periodic = 0;
     int lp = 0, lo = 0;               // stored pressure length, first stored node
     double dx = 0;
     int bcl = 0, bcr = 0;
@@ -187,7 +187,12 @@ std::complex<double> coeff(const Axis& a, int n, int dir, double scale) {
     const int N = a.N, L = a.L;
     double kap;
     bool nyquist = false;
-    if (!a.group2) {
+    if (a.periodic) {
+        // period L = N: n in [-N/2, N/2 - 1] (even N), [-(N-1)/2, (N-1)/2] (odd)
+        const int nn = n < (L + 1) / 2 ? n : n - L;
+        kap = 2.0 * M_PI * nn / (L * a.dx);
+        nyquist = (L % 2 == 0 && n == L / 2);
+    } else if (!a.group2) {
         const int nn = n <= N ? n : n - L;
         kap = 2.0 * M_PI * nn / (L * a.dx);
         nyquist = (n == N);
@@ -233,7 +238,9 @@ std::vector<double> dense_operator64(const Axis& a, int dir, double scale) {
             int src[2];
             double sg[2];
             int nimg = 0;
-            if (dir == 0) {
+            if (a.periodic) {
+                src[nimg] = j; sg[nimg++] = 1.0;
+            } else if (dir == 0) {
                 const int q = j + a.lo;
                 src[nimg] = q; sg[nimg++] = 1.0;
                 if (q > 0 && q < N) { src[nimg] = 2 * N - q; sg[nimg++] = sR; }
@@ -354,13 +361,15 @@ int build_axis(pstd_plan_s* P, int i) {
     Axis& a = P->ax[i];
     const pstd_desc& d = P->desc;
     a.N = (int)d.ncells[i];
-    a.L = 2 * a.N;
     a.dx = d.dx[i];
     a.bcl = d.bc[i][0];
     a.bcr = d.bc[i][1];
-    a.group2 = a.bcl != a.bcr;
+    a.periodic = a.bcl == PSTD_PERIODIC;
+    // period of the extension: 2N (groups I, II) or N (periodic axis)
+    a.L = a.periodic ? a.N : 2 * a.N;
+    a.group2 = !a.periodic && a.bcl != a.bcr;
     a.lo = a.bcl == PSTD_DIRICHLET ? 1 : 0;
-    const int hi = a.bcr == PSTD_DIRICHLET ? a.N - 1 : a.N;
+    const int hi = a.periodic ? a.N - 1 : (a.bcr == PSTD_DIRICHLET ? a.N - 1 : a.N);
     a.lp = hi - a.lo + 1;
     const bool fft_ok = radix_schedule(a.L, a.fft);
     a.kind = fft_ok ? 0 : (a.N <= kDenseMaxN ? 1 : 2);
@@ -590,7 +599,10 @@ int validate(const pstd_desc* d) {
         if (d->ncells[i] < 1 || d->ncells[i] > (1 << 20)) return PSTD_EINVAL;
         if (!(d->dx[i] > 0) || !std::isfinite(d->dx[i])) return PSTD_EINVAL;
         for (int s = 0; s < 2; ++s)
-            if (d->bc[i][s] != PSTD_NEUMANN && d->bc[i][s] != PSTD_DIRICHLET) return PSTD_EINVAL;
+            if (d->bc[i][s] != PSTD_NEUMANN && d->bc[i][s] != PSTD_DIRICHLET && d->bc[i][s] != PSTD_PERIODIC)
+                return PSTD_EINVAL;
+        if ((d->bc[i][0] == PSTD_PERIODIC) != (d->bc[i][1] == PSTD_PERIODIC)) return PSTD_EINVAL;
+        if (d->bc[i][0] == PSTD_PERIODIC && d->ncells[i] < 2) return PSTD_EINVAL;
         if (d->ncells[i] == 1 && d->bc[i][0] == PSTD_DIRICHLET && d->bc[i][1] == PSTD_DIRICHLET)
             return PSTD_EINVAL;
     }
@@ -600,7 +612,8 @@ int validate(const pstd_desc* d) {
     for (int i = 0; i < d->ndim; ++i) {
         const double N = (double)d->ncells[i], L = N * d->dx[i];
         double kmax;
-        if (d->bc[i][0] == PSTD_NEUMANN && d->bc[i][1] == PSTD_NEUMANN) kmax = M_PI * N / L;
+        if (d->bc[i][0] == PSTD_PERIODIC) kmax = 2.0 * M_PI * std::floor(N / 2.0) / L;
+        else if (d->bc[i][0] == PSTD_NEUMANN && d->bc[i][1] == PSTD_NEUMANN) kmax = M_PI * N / L;
         else if (d->bc[i][0] != d->bc[i][1]) kmax = M_PI * (N - 0.5) / L;
         else kmax = M_PI * (N - 1.0) / L;
         k2 += kmax * kmax;
@@ -768,7 +781,8 @@ int pstd_plan_ex(const pstd_desc* desc, void* stream, const pstd_plan_opts* opts
     for (int i = 0; i < P->ndim; ++i) {
         const int64_t N = desc->ncells[i];
         const int64_t lo = desc->bc[i][0] == PSTD_DIRICHLET ? 1 : 0;
-        const int64_t hi = desc->bc[i][1] == PSTD_DIRICHLET ? N - 1 : N;
+        const int64_t hi = desc->bc[i][0] == PSTD_PERIODIC ? N - 1
+                           : (desc->bc[i][1] == PSTD_DIRICHLET ? N - 1 : N);
         P->shape[0][i] = hi - lo + 1;
     }
     for (int f = 1; f <= P->ndim; ++f) {

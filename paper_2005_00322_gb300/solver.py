@@ -17,7 +17,10 @@ _UINIT = {"halfstep": _abi.U_HALFSTEP, "as_given": _abi.U_AS_GIVEN}
 
 
 def stored_node_range(n: int, bc) -> tuple:
-    """(first, last) stored pressure node of an axis: Dirichlet wall nodes are dropped."""
+    """(first, last) stored pressure node of an axis: Dirichlet wall nodes are
+    dropped; a periodic axis stores nodes 0..N-1."""
+    if bc[0] in ("P", _abi.PERIODIC):
+        return 0, n - 1
     lo = 1 if bc[0] in ("D", _abi.DIRICHLET) else 0
     hi = n - 1 if bc[1] in ("D", _abi.DIRICHLET) else n
     return lo, hi

@@ -72,6 +72,8 @@ def test_invalid_descriptors_rejected_before_device_work(lib):
     assert _plan_rc(lib, uinit=7) == -1
     assert _plan_rc(lib, bc=[(0, 5)]) == -1
     assert _plan_rc(lib, ncells=(1,), bc=[("D", "D")]) == -1   # no pressure node
+    assert _plan_rc(lib, bc=[("P", "N")]) == -1                # periodic needs both walls
+    assert _plan_rc(lib, ncells=(1,), bc=[("P", "P")]) == -1
 
 
 def test_stability_limit_enforced(lib):

@@ -54,6 +54,9 @@ CASES = [
     # convolution route (2N has a prime factor > 5, N > 64): power-of-two linear convolution
     ((67,), [("N", "N")]), ((97,), [("D", "N")]), ((257,), [("N", "D")]), ((130, 9), [("D", "D"), ("N", "N")]),
     ((6, 101), [("N", "D"), ("D", "D")]),
+    # periodic axes (Fourier PSTD, Section 2): register FFT, generic, convolution, dense
+    ((64,), [("P", "P")]), ((100,), [("P", "P")]), ((67,), [("P", "P")]), ((7,), [("P", "P")]),
+    ((30, 45), [("P", "P"), ("D", "N")]), ((17, 96), [("N", "N"), ("P", "P")]),
     # dense route (2N has a factor 7, 11 or 13) and tiny edge sizes
     ((7,), [("N", "D")]), ((11,), [("D", "D")]), ((13, 6), [("N", "N"), ("D", "N")]),
     ((1,), [("N", "N")]), ((1,), [("N", "D")]), ((2,), [("D", "D")]), ((2, 3), [("D", "N"), ("N", "D")]),
@@ -182,6 +185,20 @@ def test_cube256_steps_and_modal():
     s.run(p, us, w.steps - 2)
     refm = modal.separable_modal_pressure(od, _separable_factors(w, s), w.steps)
     assert rel_l2(host(p), refm) < 1e-4
+    s.close()
+
+
+def test_periodic_plane_full_run_vs_modal():
+    """2-D 128 x 96 periodic in both axes (Fourier PSTD), 1000 steps vs the modal form."""
+    ncells, bcs = (128, 96), [("P", "P"), ("P", "P")]
+    s, od = make(ncells, bcs, cfl=0.3)
+    w = inputs.small(ncells, bcs, nblobs=3, sigma_cells=3.0)
+    p0 = np.asarray(s.restrict(w.p0_full()), np.float32)
+    p, us = dev(p0), [torch.zeros(sh, device="cuda") for sh in s.shapes[1:]]
+    s.init_velocity(p, us)
+    s.run(p, us, 1000)
+    ref = modal.modal_pressure(od, p0.astype(np.float64), 1000)
+    assert rel_l2(host(p), ref) < 1e-4
     s.close()
 
 
