@@ -186,11 +186,12 @@ def reference_arm(args, w, rank: int) -> None:
 class SingleRunner:
     """One grid through Solver (pstd_plan / pstd_run)."""
 
-    def __init__(self, w, form="fft"):
+    def __init__(self, w, form="fft", persistent=False):
         import torch
         from paper_2005_00322_gb300 import Solver
         self.w = w
-        self.solver = Solver(w.ncells, w.dx, w.bc, c0=w.c0, rho0=w.rho0, cfl=w.cfl, form=form)
+        self.solver = Solver(w.ncells, w.dx, w.bc, c0=w.c0, rho0=w.rho0, cfl=w.cfl, form=form,
+                             persistent=persistent)
         self.stream = self.solver.stream
         p0 = np.asarray(self.solver.restrict(w.p0_full()), np.float32)
         self.p0 = torch.tensor(p0, device="cuda")
@@ -310,6 +311,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--leapfrog-steps", type=int, default=0, help="override the workload's step count")
+    ap.add_argument("--persistent", action="store_true",
+                    help="pstd_run as one cooperative kernel with grid barriers")
     ap.add_argument("--form", default="fft", choices=["fft", "split"],
                     help="fft: spectral FFT route; split: FP16 hi/lo tensor-core dense form")
     args = ap.parse_args()
@@ -337,7 +340,7 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
 
-    run = SingleRunner(w, args.form) if single else BatchRunner(w)
+    run = SingleRunner(w, args.form, args.persistent) if single else BatchRunner(w)
     st = run.stream
     steps_per = members_of(w)[0].steps
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
@@ -437,7 +440,8 @@ def main():
                "ncells": list(w0.ncells) if single or not isinstance(w, list) else "seeded, see inputs.plane_batch",
                "cfl": w0.cfl, "leapfrog_steps_per_bench_step": steps_per,
                "l2": "flushed (256 MB write) before each timed bench step",
-               "parallelism": "replicas" if world > 1 else "single GPU", "form": args.form}
+               "parallelism": "replicas" if world > 1 else "single GPU", "form": args.form,
+               "persistent": bool(args.persistent)}
         if single:
             cfg["bc"] = ["".join(b) for b in w.bc]
         elif not isinstance(w, list):

@@ -112,6 +112,17 @@ typedef struct {
      *    cores with FP32 accumulation (axes with N <= 1024); affects
      *    pstd_step / pstd_run only. */
     int form;
+    /* 1: pstd_run is one cooperative kernel for all its steps, the CTAs
+     * meeting at a bounded-wait grid barrier between axis passes (when every
+     * axis runs the same register-FFT schedule; otherwise ignored).  A wait
+     * that exceeds spin_limit polls (0: about a second) ends the kernel and
+     * pstd_sync returns PSTD_ETIMEOUT. */
+    int persistent;
+    int64_t spin_limit;
+    /* Testing aid: the barrier waits for this many arrivals beyond the CTAs
+     * launched, so that it cannot complete and the bounded wait must give up
+     * (exercises the PSTD_ETIMEOUT path without faulting the GPU). */
+    int withhold_arrivals;
 } pstd_plan_opts;
 
 /* pstd_plan with explicit schedule options (NULL = all automatic).
@@ -123,6 +134,10 @@ int pstd_plan_ex(const pstd_desc* desc, void* stream, const pstd_plan_opts* opts
  * sequences per CTA, CTAs per launch (-1 for an axis on the generic
  * shared-memory FFT or dense path).  Errors: PSTD_EINVAL. */
 int pstd_plan_schedule(const pstd_plan_t* plan, int axis, int out[4]);
+
+/* Whether pstd_run of this plan is one cooperative kernel: out[0] = 1 / 0,
+ * out[1] = CTAs, out[2] = threads per CTA.  Errors: PSTD_EINVAL. */
+int pstd_plan_persistent(const pstd_plan_t* plan, int out[3]);
 
 /* Shape of field 0 (p) or field i+1 (u_i) as three extents (unused axes 1).
  * Errors: PSTD_EINVAL. */
@@ -154,8 +169,9 @@ int pstd_step(pstd_plan_t* plan, float* p, float* const* u);
  * Errors: PSTD_EINVAL, PSTD_ECUDA. */
 int pstd_run(pstd_plan_t* plan, float* p, float* const* u, int64_t nsteps);
 
-/* Synchronise the plan's stream; reports device-side errors.
- * Errors: PSTD_ECUDA. */
+/* Synchronise the plan's stream; reports device-side errors, and
+ * PSTD_ETIMEOUT once (then clears it) if a bounded wait of a persistent run
+ * gave up.  Errors: PSTD_ECUDA, PSTD_ETIMEOUT. */
 int pstd_sync(pstd_plan_t* plan);
 
 /* Release the plan (synchronises its stream first).  NULL is a no-op. */

@@ -19,6 +19,7 @@ SIGNATURES = {
     "pstd_plan": (c_int, [c_void_p, c_void_p, POINTER(c_void_p)]),
     "pstd_plan_ex": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(c_void_p)]),
     "pstd_plan_schedule": (c_int, [c_void_p, c_int, POINTER(c_int)]),
+    "pstd_plan_persistent": (c_int, [c_void_p, POINTER(c_int)]),
     "pstd_field_shape": (c_int, [c_void_p, c_int, POINTER(c_int64)]),
     "pstd_field_numel": (c_int64, [c_void_p, c_int]),
     "pstd_grad": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
@@ -60,7 +61,8 @@ class PstdDesc(ctypes.Structure):
 
 class PstdPlanOpts(ctypes.Structure):
     """Mirror of pstd_plan_opts (-1 = automatic)."""
-    _fields_ = [("variant", c_int * 3), ("seqs_per_cta", c_int * 3), ("form", c_int)]
+    _fields_ = [("variant", c_int * 3), ("seqs_per_cta", c_int * 3), ("form", c_int),
+                ("persistent", c_int), ("spin_limit", c_int64), ("withhold_arrivals", c_int)]
 
 
 class PstdError(RuntimeError):

@@ -39,14 +39,20 @@ cudaError_t wsmall_step(int L, int V, bool s, const WLaunch& g, cudaStream_t st,
 cudaError_t wsmall_grad(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WGrad& a);
 cudaError_t wsmall_smem(int L, int V, int bytes);
 bool wsmall_twiddles(int L, int V, std::vector<float2>& out);
+cudaError_t wsmall_persist(int L, int V, const WLaunch& g, cudaStream_t st, const PersistArgs& a);
+cudaError_t wsmall_persist_blocks(int L, int V, int threads, size_t smem, int* blocks);
 cudaError_t w512_step(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WStep& a);
 cudaError_t w512_grad(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WGrad& a);
 cudaError_t w512_smem(int L, int V, int bytes);
 bool w512_twiddles(int L, int V, std::vector<float2>& out);
+cudaError_t w512_persist(int L, int V, const WLaunch& g, cudaStream_t st, const PersistArgs& a);
+cudaError_t w512_persist_blocks(int L, int V, int threads, size_t smem, int* blocks);
 cudaError_t w1024_step(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WStep& a);
 cudaError_t w1024_grad(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WGrad& a);
 cudaError_t w1024_smem(int L, int V, int bytes);
 bool w1024_twiddles(int L, int V, std::vector<float2>& out);
+cudaError_t w1024_persist(int L, int V, const WLaunch& g, cudaStream_t st, const PersistArgs& a);
+cudaError_t w1024_persist_blocks(int L, int V, int threads, size_t smem, int* blocks);
 }  // namespace pstd
 
 using pstd::FftPlan;
@@ -57,6 +63,7 @@ using pstd::WAxis;
 using pstd::WGrad;
 using pstd::WLaunch;
 using pstd::WStep;
+using pstd::PersistArgs;
 
 namespace {
 
@@ -113,6 +120,16 @@ cudaError_t wsmem(int L, int V, int bytes) {
     if (L == 512 || L == 384) return pstd::w512_smem(L, V, bytes);
     return pstd::wsmall_smem(L, V, bytes);
 }
+cudaError_t wpersist(int L, int V, const WLaunch& g, cudaStream_t st, const pstd::PersistArgs& a) {
+    if (L >= 1024 || L == 768) return pstd::w1024_persist(L, V, g, st, a);
+    if (L == 512 || L == 384) return pstd::w512_persist(L, V, g, st, a);
+    return pstd::wsmall_persist(L, V, g, st, a);
+}
+cudaError_t wpersist_blocks(int L, int V, int threads, size_t smem, int* blocks) {
+    if (L >= 1024 || L == 768) return pstd::w1024_persist_blocks(L, V, threads, smem, blocks);
+    if (L == 512 || L == 384) return pstd::w512_persist_blocks(L, V, threads, smem, blocks);
+    return pstd::wsmall_persist_blocks(L, V, threads, smem, blocks);
+}
 bool wtw(int L, int V, std::vector<float2>& out) {
     if (L >= 1024 || L == 768) return pstd::w1024_twiddles(L, V, out);
     if (L == 512 || L == 384) return pstd::w512_twiddles(L, V, out);
@@ -168,7 +185,10 @@ bool radix_schedule(int L, FftPlan& P) {
 
 struct pstd_plan_s {
     pstd_desc desc{};
-    pstd_plan_opts opts{{-1, -1, -1}, {-1, -1, -1}, 0};
+    pstd_plan_opts opts{{-1, -1, -1}, {-1, -1, -1}, 0, 0, 0, 0};
+    unsigned* d_sync = nullptr;       // grid barrier: count, generation, status
+    int persist_ok = 0;
+    WLaunch pgeo{};
     cudaStream_t stream = nullptr;
     int ndim = 0;
     int64_t shape[4][3] = {};
@@ -586,6 +606,7 @@ void free_plan_memory(pstd_plan_s* P) {
         }
     }
     cudaFree(P->d_S);
+    cudaFree(P->d_sync);
     for (auto& g : P->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
 }
@@ -747,6 +768,14 @@ int pstd_plan(const pstd_desc* desc, void* stream, pstd_plan_t** out) {
     return pstd_plan_ex(desc, stream, nullptr, out);
 }
 
+int pstd_plan_persistent(const pstd_plan_t* P, int out[3]) {
+    if (!P || !out) return PSTD_EINVAL;
+    out[0] = P->persist_ok;
+    out[1] = (int)P->pgeo.grid;
+    out[2] = P->pgeo.threads;
+    return PSTD_OK;
+}
+
 int pstd_plan_schedule(const pstd_plan_t* P, int axis, int out[4]) {
     if (!P || !out || axis < 0 || axis >= P->ndim) return PSTD_EINVAL;
     const Axis& A = P->ax[axis];
@@ -815,6 +844,37 @@ int pstd_plan_ex(const pstd_desc* desc, void* stream, const pstd_plan_opts* opts
             if (e != cudaSuccess) rc = cuda_fail(e, "cudaFuncSetAttribute(register-FFT pass)");
         }
     }
+    // persistent run: every axis on the same register-FFT schedule and CTA size
+    if (rc == PSTD_OK && P->opts.persistent) {
+        bool same = P->opts.form == 0;
+        for (int i = 0; i < P->ndim && same; ++i)
+            same = P->ax[i].wl > 0 && P->ax[i].L == P->ax[0].L && P->ax[i].wv == P->ax[0].wv &&
+                   P->ax[i].wgeo.threads == P->ax[0].wgeo.threads;
+        if (same) {
+            size_t smem = 0;
+            int64_t items = 0;
+            for (int i = 0; i < P->ndim; ++i) {
+                smem = P->ax[i].wgeo.smem > smem ? P->ax[i].wgeo.smem : smem;
+                items = (int64_t)P->ax[i].wgeo.grid > items ? (int64_t)P->ax[i].wgeo.grid : items;
+            }
+            int per_sm = 0, dev = 0, nsm = 0;
+            cudaError_t e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess)
+                e = wpersist_blocks(P->ax[0].L, P->ax[0].wv, P->ax[0].wgeo.threads, smem, &per_sm);
+            if (e == cudaSuccess) e = cudaMalloc((void**)&P->d_sync, 4 * sizeof(unsigned));
+            if (e == cudaSuccess) e = cudaMemset(P->d_sync, 0, 4 * sizeof(unsigned));
+            if (e != cudaSuccess) rc = cuda_fail(e, "persistent set-up");
+            else if (per_sm > 0) {
+                int64_t grid = (int64_t)per_sm * nsm;
+                if (grid > items) grid = items;
+                P->pgeo.grid = (unsigned)grid;
+                P->pgeo.threads = P->ax[0].wgeo.threads;
+                P->pgeo.smem = smem;
+                P->persist_ok = 1;
+            }
+        }
+    }
     if (rc != PSTD_OK) {
         free_plan_memory(P);
         delete P;
@@ -870,6 +930,33 @@ int pstd_run(pstd_plan_t* P, float* p, float* const* u, int64_t nsteps) {
     for (int a = 0; a < P->ndim; ++a)
         if (!u[a]) return PSTD_EINVAL;
     P->last_launches = 0;
+    if (P->persist_ok && nsteps > 0) {
+        PersistArgs pa{};
+        pa.ndim = P->ndim;
+        pa.nsteps = nsteps;
+        for (int a = 0; a < P->ndim; ++a) {
+            Axis& A = P->ax[a];
+            WStep& w = pa.ax[a];
+            w.ax = A.wax;
+            w.fP = A.d_f[OP_STEP_P];
+            w.fU = A.d_f[OP_STEP_U];
+            w.p = p;
+            w.u = u[a];
+            w.acc_in = (a == P->ndim - 1) ? p : P->d_S;
+            w.acc_out = (a == 0) ? p : P->d_S;
+            pa.strided[a] = A.strided ? 1 : 0;
+            pa.items[a] = A.wgeo.grid;
+        }
+        pa.sync.count = P->d_sync;
+        pa.sync.gen = P->d_sync + 1;
+        pa.sync.status = (int*)(P->d_sync + 2);
+        pa.sync.expected = P->pgeo.grid + (unsigned)(P->opts.withhold_arrivals > 0 ? P->opts.withhold_arrivals : 0);
+        pa.sync.spin_limit = P->opts.spin_limit > 0 ? P->opts.spin_limit : 2000000LL;   // ~0.2-1 s of polls
+        CK(cudaMemsetAsync(P->d_sync, 0, sizeof(unsigned), P->stream));   // arrival count
+        CK(wpersist(P->ax[0].L, P->ax[0].wv, P->pgeo, P->stream, pa));
+        P->last_launches = 1;
+        return PSTD_OK;
+    }
     int64_t done = 0;
     if (P->stream != nullptr && nsteps >= kGraphSteps) {
         // find or record the graph of kGraphSteps steps for this pointer set
@@ -922,6 +1009,14 @@ int pstd_sync(pstd_plan_t* P) {
     if (!P) return PSTD_EINVAL;
     CK(cudaStreamSynchronize(P->stream));
     CK(cudaGetLastError());
+    if (P->d_sync) {
+        int status = 0;
+        CK(cudaMemcpy(&status, P->d_sync + 2, sizeof(int), cudaMemcpyDeviceToHost));
+        if (status != 0) {
+            CK(cudaMemset(P->d_sync, 0, 4 * sizeof(unsigned)));
+            return PSTD_ETIMEOUT;
+        }
+    }
     return PSTD_OK;
 }
 

@@ -5,6 +5,7 @@
 
 #include <vector>
 
+#include "pstd_persist.cuh"
 #include "pstd_wcta.cuh"
 
 namespace pstd {
@@ -34,6 +35,13 @@ __global__ void __launch_bounds__(256) k_wgrad_s(WGrad a) {
     wk::grad_strided<wf::Sched<L, V>>(a, blockIdx.x, wsm, threadIdx.x, blockDim.x);
 }
 
+// One cooperative launch for a whole run (pstd_persist.cuh).
+template <int L, int V>
+__global__ void __launch_bounds__(256) k_persist(PersistArgs a) {
+    extern __shared__ float4 wsm4[];
+    persistent_run<wf::Sched<L, V>>(a, (float2*)wsm4);
+}
+
 // Launch geometry shared by the host plan and the launchers.
 struct WLaunch {
     unsigned grid;
@@ -54,8 +62,28 @@ cudaError_t wlaunch_grad(bool strided, const WLaunch& g, cudaStream_t st, const 
     return cudaGetLastError();
 }
 template <int L, int V>
+cudaError_t wlaunch_persist(const WLaunch& g, cudaStream_t st, const PersistArgs& a) {
+    void* args[] = {(void*)&a};
+    return cudaLaunchCooperativeKernel((const void*)k_persist<L, V>, dim3(g.grid), dim3(g.threads), args, g.smem,
+                                       st);
+}
+template <int L, int V>
+cudaError_t wpersist_blocks(int threads, size_t smem, int* blocks) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_persist<L, V>, threads, smem);
+}
+// Dynamic shared-memory limit of one kernel: `bytes` minus its static share.
+template <class K>
+cudaError_t wset_one(K* kernel, int bytes) {
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                bytes - (int)fa.sharedSizeBytes);
+}
+template <int L, int V>
 cudaError_t wset_smem(int bytes) {
     cudaError_t e;
+    if ((e = wset_one(k_persist<L, V>, bytes))) return e;
     if ((e = cudaFuncSetAttribute(k_wstep_s<L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
     if ((e = cudaFuncSetAttribute(k_wstep_c<L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
     if ((e = cudaFuncSetAttribute(k_wgrad_s<L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
@@ -88,11 +116,19 @@ void wtwiddles(std::vector<float2>& out) {
     }                                                                                                    \
     bool NAME##_twiddles(int L, int V, std::vector<float2>& out) {                                       \
         switch (2 * L + V) { LIST(PSTD_WCASE_TW) default: return false; }                                \
+    }                                                                                                    \
+    cudaError_t NAME##_persist(int L, int V, const WLaunch& g, cudaStream_t st, const PersistArgs& a) {  \
+        switch (2 * L + V) { LIST(PSTD_WCASE_PERSIST) default: return cudaErrorInvalidValue; }           \
+    }                                                                                                    \
+    cudaError_t NAME##_persist_blocks(int L, int V, int threads, size_t smem, int* blocks) {             \
+        switch (2 * L + V) { LIST(PSTD_WCASE_PBLOCKS) default: return cudaErrorInvalidValue; }           \
     }
 #define PSTD_WCASE_STEP(LL, VV) case 2 * LL + VV: return wlaunch_step<LL, VV>(s, g, st, a);
 #define PSTD_WCASE_GRAD(LL, VV) case 2 * LL + VV: return wlaunch_grad<LL, VV>(s, g, st, a);
 #define PSTD_WCASE_SMEM(LL, VV) case 2 * LL + VV: return wset_smem<LL, VV>(bytes);
 #define PSTD_WCASE_TW(LL, VV) case 2 * LL + VV: wtwiddles<LL, VV>(out); return true;
+#define PSTD_WCASE_PERSIST(LL, VV) case 2 * LL + VV: return wlaunch_persist<LL, VV>(g, st, a);
+#define PSTD_WCASE_PBLOCKS(LL, VV) case 2 * LL + VV: return wpersist_blocks<LL, VV>(threads, smem, blocks);
 
 // Lanes per sequence of the latency schedule Sched<L, 1> (0: none).
 inline int wlanes_latency(int L) {

@@ -35,7 +35,8 @@ class Solver:
     """
 
     def __init__(self, ncells, dx, bc, c0=1500.0, rho0=1000.0, dt=None, cfl=None,
-                 uinit="halfstep", device=None, stream=None, schedule=None, form="fft"):
+                 uinit="halfstep", device=None, stream=None, schedule=None, form="fft",
+                 persistent=False, spin_limit=0, withhold_arrivals=0):
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the PSTD library runs on the GPU only")
         self.lib = _abi.load()
@@ -55,7 +56,7 @@ class Solver:
         opts = None
         if form not in ("fft", "split"):
             raise ValueError("form is 'fft' or 'split'")
-        if schedule is not None or form != "fft":
+        if schedule is not None or form != "fft" or persistent or withhold_arrivals:
             # schedule: per axis (variant, seqs_per_cta), None entries automatic
             opts = _abi.PstdPlanOpts()
             for i in range(3):
@@ -63,6 +64,9 @@ class Solver:
                 opts.variant[i] = -1 if v is None else int(v)
                 opts.seqs_per_cta[i] = -1 if q is None else int(q)
             opts.form = 1 if form == "split" else 0
+            opts.persistent = 1 if persistent else 0
+            opts.spin_limit = int(spin_limit)
+            opts.withhold_arrivals = int(withhold_arrivals)
         h = ctypes.c_void_p()
         rc = self.lib.pstd_plan_ex(ctypes.byref(self._desc), ctypes.c_void_p(self.stream.cuda_stream),
                                    ctypes.byref(opts) if opts is not None else None, ctypes.byref(h))
@@ -96,6 +100,12 @@ class Solver:
             _abi.check(self.lib, self.lib.pstd_plan_schedule(self._h, a, v), "pstd_plan_schedule")
             out.append(tuple(v))
         return out
+
+    def persistent(self):
+        """(enabled, CTAs, threads) of the one-kernel pstd_run."""
+        v = (ctypes.c_int * 3)()
+        _abi.check(self.lib, self.lib.pstd_plan_persistent(self._h, v), "pstd_plan_persistent")
+        return bool(v[0]), int(v[1]), int(v[2])
 
     def last_launch_count(self) -> int:
         return int(self.lib.pstd_last_launch_count(self._h))
