@@ -492,13 +492,17 @@ int build_axis(pstd_plan_s* P, int i) {
     int V = 0;
     int os = P->opts.seqs_per_cta[i];
     const int ov = P->opts.variant[i];
-    if (ov == 1 || (ov < 0 && pstd::wlanes_latency(a.L) > 0)) {
+    if (ov == 2) {
+        if (pstd::wlanes_v2(a.L) == 0) return PSTD_EINVAL;
+        V = 2;
+        T = pstd::wlanes_v2(a.L);
+    } else if (ov == 1 || (ov < 0 && pstd::wlanes_latency(a.L) > 0)) {
         if (pstd::wlanes_latency(a.L) == 0) return PSTD_EINVAL;
         V = 1;
         T = pstd::wlanes_latency(a.L);
     }
     if (os == 0 || os > 256 || (os > 0 && (os & (os - 1)))) return PSTD_EINVAL;
-    if (os < 0 && V == 1 && T <= 128 && (a.nlines + 1) / 2 >= 2 * 2 * 152) os = 2;
+    if (os < 0 && V >= 1 && T <= 128 && (a.nlines + 1) / 2 >= 2 * 2 * 152) os = 2;
     if (a.kind == 0 && T > 0) {
         std::vector<float2> wt;
         if (!wtw(a.L, V, wt)) return PSTD_EUNSUPPORTED;
@@ -518,7 +522,7 @@ int build_axis(pstd_plan_s* P, int i) {
         a.strided = a.inner > 1;
         const int64_t nseq = (a.nlines + 1) / 2;
         const int64_t want = 2 * 152;
-        int threads = V == 1 ? T : 128;
+        int threads = V >= 1 ? T : 128;
         if (os > 0) {
             threads = os * T;
             if (threads < 32 || threads > 256) return PSTD_EINVAL;

@@ -61,6 +61,21 @@ PSTD_HD void async_copy4(void* sdst, const void* gsrc) {
     *(float*)sdst = *(const float*)gsrc;
 #endif
 }
+// Programmatic dependent launch: a pass launched with the programmatic-
+// serialisation attribute may start while the previous pass drains; it loads
+// its constant tables first and waits here before touching any field.
+PSTD_HD void pdl_wait() {
+#ifdef __CUDA_ARCH__
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+#endif
+}
+// Let the next pass be scheduled (called once this CTA's work is done).
+PSTD_HD void pdl_trigger() {
+#ifdef __CUDA_ARCH__
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+#endif
+}
+
 // Wait for this thread's copies; a CTA barrier must follow before others read.
 PSTD_HD void async_wait_all() {
 #ifdef __CUDA_ARCH__
@@ -201,7 +216,7 @@ PSTD_HD void derivative(float2 (&v)[S::E], int t, float2* sm, const WAxis& A, co
 // Tables of one derivative for schedule S (registers for the latency
 // schedules, direct access otherwise).
 template <class S>
-using TablesOf = typename std::conditional<S::V == 1, TablesInRegs<S>, TablesDirect<S>>::type;
+using TablesOf = typename std::conditional<S::V >= 1, TablesInRegs<S>, TablesDirect<S>>::type;
 
 template <class S>
 PSTD_HD TablesOf<S> tables(const WAxis& A, const float2* f0, const float2* f1, int t) {
@@ -211,7 +226,7 @@ PSTD_HD TablesOf<S> tables(const WAxis& A, const float2* f0, const float2* f1, i
     tb.f1 = f1;
     tb.shift = A.shift;
     tb.t = t;
-    if constexpr (S::V == 1) tb.load(A.group2 != 0);
+    if constexpr (S::V >= 1) tb.load(A.group2 != 0);
     return tb;
 }
 
@@ -230,7 +245,7 @@ PSTD_HD void lane_of(int tid, int& seq, int& t) {
 template <class S>
 PSTD_HD float2* stage_tables(WAxis& A, const float2*& f1, const float2*& f2, float2* dst, int tid,
                              int nthr) {
-    if constexpr (S::V == 1) return dst;   // latency schedules keep tables in registers
+    if constexpr (S::V >= 1) return dst;   // latency schedules keep tables in registers
     constexpr int ntw = (wf::tw_total<S>() + 1) & ~1;
     constexpr int L = S::L;
     float2* p = dst;
@@ -264,6 +279,7 @@ PSTD_HD void step_contig(const WStep& a, int64_t block, float2* smem, int tid, i
     const float2* fU = a.fU;
     float2* bufs = stage_tables<S>(A, fP, fU, smem, tid, nthr);
     const auto tab = tables<S>(A, fP, fU, t);
+    pdl_wait();
     const int64_t seq = block * A.seqs + sq;
     const int64_t la = 2 * seq, lb = 2 * seq + 1;
     const bool va = la < A.nlines, vb = lb < A.nlines;
@@ -315,6 +331,7 @@ PSTD_HD void step_contig(const WStep& a, int64_t block, float2* smem, int tid, i
             if (vb) ob[i] = ao[e].y + v[e].y;
         }
     }
+    pdl_trigger();
 }
 
 template <class S>
@@ -329,6 +346,7 @@ PSTD_HD void grad_contig(const WGrad& a, int64_t block, float2* smem, int tid, i
     const auto tab = tables<S>(A, a.dir == 0 ? f : nullptr, a.dir == 0 ? nullptr : f, t);
     async_wait_all();
     PSTD_SYNCCTA();
+    pdl_wait();
     const int64_t seq = block * A.seqs + sq;
     const int64_t la = 2 * seq, lb = 2 * seq + 1;
     const bool va = la < A.nlines, vb = lb < A.nlines;
@@ -416,6 +434,7 @@ PSTD_HD void step_strided(const WStep& a, int64_t block, float2* smem0, int tid,
     float* rawP = (float*)(smem + (size_t)A.seqs * wf::seq_words<S::L>());
     float* rawU = rawP + (size_t)A.G * row_stride(lp);
     float* rawA = sep ? rawU + (size_t)A.G * row_stride(N) : rawP;
+    pdl_wait();
     tile_load(a.p, lp, A, o, i0, Gv, rawP, tid, nthr);
     tile_load(a.u, N, A, o, i0, Gv, rawU, tid, nthr);
     if (sep) tile_load(a.acc_in, lp, A, o, i0, Gv, rawA, tid, nthr);
@@ -461,6 +480,7 @@ PSTD_HD void step_strided(const WStep& a, int64_t block, float2* smem0, int tid,
     PSTD_SYNCCTA();
     tile_store(a.u, N, A, o, i0, Gv, rawU, tid, nthr);
     tile_store(a.acc_out, lp, A, o, i0, Gv, rawA, tid, nthr);
+    pdl_trigger();
 }
 
 template <class S>
@@ -480,6 +500,7 @@ PSTD_HD void grad_strided(const WGrad& a, int64_t block, float2* smem0, int tid,
     const int nout = a.dir == 0 ? A.N : A.lp;
     float* rawI = (float*)(smem + (size_t)A.seqs * wf::seq_words<S::L>());
     float* rawO = rawI + (size_t)A.G * row_stride(nin);
+    pdl_wait();
     tile_load(a.in, nin, A, o, i0, Gv, rawI, tid, nthr);
     if (a.accumulate) tile_load(a.out, nout, A, o, i0, Gv, rawO, tid, nthr);
     async_wait_all();

@@ -49,11 +49,27 @@ struct WLaunch {
     size_t smem;
 };
 
+// Launch with programmatic stream serialisation (the kernels wait with
+// griddepcontrol.wait before reading fields), so that a pass's launch and
+// table loads overlap the drain of the previous one.
+template <class... Args>
+cudaError_t launch_pdl(void (*kernel)(Args...), const WLaunch& g, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(g.grid);
+    cfg.blockDim = dim3(g.threads);
+    cfg.dynamicSmemBytes = g.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <int L, int V>
 cudaError_t wlaunch_step(bool strided, const WLaunch& g, cudaStream_t st, const WStep& a) {
-    if (strided) k_wstep_s<L, V><<<g.grid, g.threads, g.smem, st>>>(a);
-    else k_wstep_c<L, V><<<g.grid, g.threads, g.smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(strided ? k_wstep_s<L, V> : k_wstep_c<L, V>, g, st, a);
 }
 template <int L, int V>
 cudaError_t wlaunch_grad(bool strided, const WLaunch& g, cudaStream_t st, const WGrad& a) {
@@ -129,6 +145,9 @@ void wtwiddles(std::vector<float2>& out) {
 #define PSTD_WCASE_TW(LL, VV) case 2 * LL + VV: wtwiddles<LL, VV>(out); return true;
 #define PSTD_WCASE_PERSIST(LL, VV) case 2 * LL + VV: return wlaunch_persist<LL, VV>(g, st, a);
 #define PSTD_WCASE_PBLOCKS(LL, VV) case 2 * LL + VV: return wpersist_blocks<LL, VV>(threads, smem, blocks);
+
+// Lanes per sequence of Sched<L, 2> (fewer, wider passes; 0: none).
+inline int wlanes_v2(int L) { return L == 1024 ? 64 : 0; }
 
 // Lanes per sequence of the latency schedule Sched<L, 1> (0: none).
 inline int wlanes_latency(int L) {
