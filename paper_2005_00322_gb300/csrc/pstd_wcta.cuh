@@ -386,25 +386,34 @@ PSTD_HD void tile_of(const WAxis& A, int64_t block, int64_t& o, int64_t& i0, int
 // transposed staging).
 PSTD_HD int row_stride(int len) { return len | 1; }
 
+// G is a power of two: item idx is (position idx >> log2 G, line idx & (G-1)).
+PSTD_HD int log2_pow2(int G) {
+    int s = 0;
+    while ((1 << s) < G) ++s;
+    return s;
+}
+
 PSTD_HD void tile_load(const float* f, int len, const WAxis& A, int64_t o, int64_t i0, int Gv,
                        float* raw, int tid, int nthr) {
     const int rs = row_stride(len);
-    const int64_t base = o * (int64_t)len * A.inner + i0;
-    const int total = len * Gv;
+    const int gs = log2_pow2(A.G), gm = A.G - 1;
+    const float* base = f + o * (int64_t)len * A.inner + i0;
+    const int total = len << gs;
     for (int idx = tid; idx < total; idx += nthr) {
-        const int pos = idx / Gv, g = idx - pos * Gv;
-        async_copy4(&raw[g * rs + pos], &f[base + (int64_t)pos * A.inner + g]);
+        const int pos = idx >> gs, g = idx & gm;
+        if (g < Gv) async_copy4(&raw[g * rs + pos], &base[(int64_t)pos * A.inner + g]);
     }
 }
 
 PSTD_HD void tile_store(float* f, int len, const WAxis& A, int64_t o, int64_t i0, int Gv,
                         const float* raw, int tid, int nthr) {
     const int rs = row_stride(len);
-    const int64_t base = o * (int64_t)len * A.inner + i0;
-    const int total = len * Gv;
+    const int gs = log2_pow2(A.G), gm = A.G - 1;
+    float* base = f + o * (int64_t)len * A.inner + i0;
+    const int total = len << gs;
     for (int idx = tid; idx < total; idx += nthr) {
-        const int pos = idx / Gv, g = idx - pos * Gv;
-        f[base + (int64_t)pos * A.inner + g] = raw[g * rs + pos];
+        const int pos = idx >> gs, g = idx & gm;
+        if (g < Gv) base[(int64_t)pos * A.inner + g] = raw[g * rs + pos];
     }
 }
 
