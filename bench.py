@@ -183,6 +183,21 @@ def reference_arm(args, w, rank: int) -> None:
     print(json.dumps(line), flush=True)
 
 
+def rank_max(x: float, dist, device) -> float:
+    """The largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Units processed by all ranks divided by the slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
 class SingleRunner:
     """One grid through Solver (pstd_plan / pstd_run)."""
 
@@ -368,13 +383,9 @@ def main():
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    t = sum(times)
-    if dist:
-        tt = torch.tensor([t], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = rank_max(sum(times), dist, "cuda")
     updates = run.cells * steps_per * args.steps * world
-    value = updates / t
+    value = whole_job_rate(run.cells * steps_per * args.steps, world, t)
 
     # dominant kernel: the fused axis pass; mean duration per launch from
     # events around direct (non-graph) leapfrog steps on the plan's stream
@@ -420,11 +431,7 @@ def main():
     for _ in range(args.steps):
         run.step_e2e()
         torch.cuda.synchronize()
-    te = time.perf_counter() - t0
-    if dist:
-        tt = torch.tensor([te], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = float(tt.item())
+    te = rank_max(time.perf_counter() - t0, dist, "cuda")
     e2e = {"value": updates / te, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     cpu = None
