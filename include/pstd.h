@@ -267,6 +267,85 @@ int pstd_reflection_combos(const pstd_desc* tmpl, const double* refl, pstd_desc*
 int pstd_step_noalloc(const pstd_desc* desc, float* p, float* const* u, int64_t nsteps,
                       void* stream);
 
+/* ---- Learned spectral operator (not in the paper) ------------------------- */
+/* Kernels of a spectral neural operator that maps an initial pressure on a
+ * box to the pressure a fixed number of leapfrog steps later.  Its spectral
+ * layers work in the truncated T1 basis of each axis (Table 2), so they keep
+ * the walls.  Every call below enqueues on `stream` (a cudaStream_t, NULL =
+ * legacy default stream), takes device pointers to FP32 buffers the caller
+ * owns, and returns PSTD_OK, PSTD_EINVAL (bad pointer or size; nothing is
+ * launched) or PSTD_ECUDA (launch failed). */
+
+/* C[b] = alpha A[b] B[b] + beta C[b] for b < batch, A[b] M x K, B[b] K x N,
+ * element (m, k) of A[b] at A + b sAb + m sAm + k sAk (strides in elements,
+ * non-negative, any layout; B and C alike).  beta == 0 ignores C's old
+ * contents.  A second batch level (batch2 > 1; 0 or 1 = none) adds
+ * b2 sAb2 / sBb2 / sCb2 for b2 < batch2, and its last index uses K_last
+ * (0 <= K_last <= K) instead of K: a split of a long reduction into batch2
+ * chunks whose partial products the caller sums.  batch * batch2 <= 65535,
+ * ceil(M / 256) <= 65535; A and B may be NULL when K == 0. */
+typedef struct {
+    int64_t batch;
+    int M, N, K;
+    const float* A;
+    int64_t sAb, sAm, sAk;
+    const float* B;
+    int64_t sBb, sBk, sBn;
+    float* C;
+    int64_t sCb, sCm, sCn;
+    float alpha, beta;
+    int64_t batch2;
+    int64_t sAb2, sBb2, sCb2;
+    int K_last;
+} pstd_gemm_desc;
+int pstd_nn_gemm(const pstd_gemm_desc* d, void* stream);
+
+/* Tensors below are [B][C][P] (B samples, C channels, P points) or [B][P];
+ * bias_act, lift and proj_bwd need B C <= 65535, proj B <= 65535.
+ * y = act(x + bias[c]) with act 0 = identity, 1 = relu; bias may be NULL. */
+int pstd_nn_bias_act(const float* x, const float* bias, float* y, int64_t B, int C, int64_t P, int act,
+                     void* stream);
+/* dx = dy where act is identity or pre > 0, else 0 (n elements; dx may alias dy). */
+int pstd_nn_act_bwd(const float* dy, const float* pre, float* dx, int64_t n, int act, void* stream);
+/* v[b][c][i] = w[c] p[b][i] + bias[c]  (lifting 1 -> C channels). */
+int pstd_nn_lift(const float* p, const float* w, const float* bias, float* v, int64_t B, int C, int64_t P,
+                 void* stream);
+/* out[b][i] = sum_c w[c] v[b][c][i] + bias[0]  (projection C -> 1). */
+int pstd_nn_proj(const float* v, const float* w, const float* bias, float* out, int64_t B, int C, int64_t P,
+                 void* stream);
+/* dv[b][c][i] = w[c] dout[b][i]  (adjoint of the projection). */
+int pstd_nn_proj_bwd(const float* dout, const float* w, float* dv, int64_t B, int C, int64_t P, void* stream);
+/* g[c] = sum_{b,i} x[b][c][i] y[.]: y indexed [b][c][i] when y_has_channels,
+ * [b][i] otherwise, and taken as 1 when NULL.  Sums in FP64. */
+int pstd_nn_chan_dot(const float* x, const float* y, int y_has_channels, float* g, int64_t B, int C, int64_t P,
+                     void* stream);
+/* out[j] = sum_b x[b][j], j < n, summed in FP64. */
+int pstd_nn_sum_lead(const float* x, float* out, int64_t B, int64_t n, void* stream);
+/* Adam with bias correction (Kingma & Ba 2015) on n parameters, step >= 1. */
+int pstd_nn_adam(float* w, const float* g, float* m, float* v, int64_t n, float lr, float beta1, float beta2,
+                 float eps, int64_t step, void* stream);
+/* loss[0] = mean (out - target)^2 over n values; dout = (2/n)(out - target)
+ * unless dout is NULL. */
+int pstd_nn_mse(const float* out, const float* target, float* dout, float* loss, int64_t n, void* stream);
+/* err[b] = ||a_b - ref_b||_2 / ||ref_b||_2 per sample of P values (FP64 sums;
+ * the plain norm of the difference where ref_b is zero). */
+int pstd_nn_rel_err(const float* a, const float* ref, float* err, int64_t B, int64_t P, void* stream);
+/* rms[b] = sqrt(mean_i x[b][i]^2) over P values per sample (FP64 sum). */
+int pstd_nn_row_rms(const float* x, float* rms, int64_t B, int64_t P, void* stream);
+/* y[b][i] = x[b][i] / s[b] (mode 0; 0 where s[b] == 0) or x[b][i] s[b]
+ * (mode 1); y may alias x.  B <= 65535. */
+int pstd_nn_row_scale(const float* x, const float* s, float* y, int64_t B, int64_t P, int mode, void* stream);
+/* dst = src rounded to the nearest bfloat16, ties to even, stored as FP32. */
+int pstd_nn_round_bf16(const float* src, float* dst, int64_t n, void* stream);
+
+/* Host only.  The first K modes of the T1 transform of an axis of `ncells`
+ * cells with walls (bc_left, bc_right) in {PSTD_NEUMANN, PSTD_DIRICHLET}, on
+ * its lp stored pressure nodes (lp = N+1, N, N, N-1 for NN, ND, DN, DD):
+ * T (K x lp, row-major) the unnormalised forward transform's first K rows and
+ * I (lp x K) the first K columns of its inverse (Eq. inverse_transforms).
+ * Host buffers owned by the caller.  Errors: PSTD_EINVAL (K > lp, bad wall). */
+int pstd_sno_basis(int ncells, int bc_left, int bc_right, int K, float* T, float* I);
+
 #ifdef __cplusplus
 }
 #endif

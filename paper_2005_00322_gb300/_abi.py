@@ -4,7 +4,7 @@ from __future__ import annotations
 import ctypes
 import os
 
-from ctypes import POINTER, c_char_p, c_double, c_int, c_int64, c_void_p
+from ctypes import POINTER, c_char_p, c_double, c_float, c_int, c_int64, c_void_p
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libpstd.so")
 
@@ -42,6 +42,22 @@ SIGNATURES = {
     "pstd_batch_last_launch_count": (c_int64, [c_void_p]),
     "pstd_reflection_combos": (c_int, [c_void_p, POINTER(c_double), c_void_p, POINTER(c_double)]),
     "pstd_step_noalloc": (c_int, [c_void_p, c_void_p, POINTER(c_void_p), c_int64, c_void_p]),
+    "pstd_nn_gemm": (c_int, [c_void_p, c_void_p]),
+    "pstd_nn_bias_act": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int, c_int64, c_int, c_void_p]),
+    "pstd_nn_act_bwd": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int, c_void_p]),
+    "pstd_nn_lift": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int, c_int64, c_void_p]),
+    "pstd_nn_proj": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int, c_int64, c_void_p]),
+    "pstd_nn_proj_bwd": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int, c_int64, c_void_p]),
+    "pstd_nn_chan_dot": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int64, c_int, c_int64, c_void_p]),
+    "pstd_nn_sum_lead": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_void_p]),
+    "pstd_nn_adam": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_float, c_float, c_float,
+                             c_float, c_int64, c_void_p]),
+    "pstd_nn_mse": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
+    "pstd_nn_rel_err": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_void_p]),
+    "pstd_nn_round_bf16": (c_int, [c_void_p, c_void_p, c_int64, c_void_p]),
+    "pstd_nn_row_rms": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_void_p]),
+    "pstd_nn_row_scale": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int, c_void_p]),
+    "pstd_sno_basis": (c_int, [c_int, c_int, c_int, c_int, POINTER(c_float), POINTER(c_float)]),
 }
 
 
@@ -57,6 +73,16 @@ class PstdDesc(ctypes.Structure):
         ("dt", c_double),
         ("uinit", c_int),
     ]
+
+
+class PstdGemmDesc(ctypes.Structure):
+    """Mirror of pstd_gemm_desc."""
+    _fields_ = [("batch", c_int64), ("M", c_int), ("N", c_int), ("K", c_int),
+                ("A", c_void_p), ("sAb", c_int64), ("sAm", c_int64), ("sAk", c_int64),
+                ("B", c_void_p), ("sBb", c_int64), ("sBk", c_int64), ("sBn", c_int64),
+                ("C", c_void_p), ("sCb", c_int64), ("sCm", c_int64), ("sCn", c_int64),
+                ("alpha", c_float), ("beta", c_float),
+                ("batch2", c_int64), ("sAb2", c_int64), ("sBb2", c_int64), ("sCb2", c_int64), ("K_last", c_int)]
 
 
 class PstdPlanOpts(ctypes.Structure):

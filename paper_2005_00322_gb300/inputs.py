@@ -150,3 +150,29 @@ def small(ncells, bc, cfl=0.3, steps=20, seed=0, nblobs=2, sigma_cells=2.0) -> W
 def random_field(shape, seed: int) -> np.ndarray:
     """Standard-normal FP64 field (for per-step and transform parity cases)."""
     return np.random.default_rng(seed).standard_normal(shape)
+
+
+def plane128_nn_dd(steps: int = 200) -> Workload:
+    """The learned operator's box: 128 x 128 cells, Neumann walls on x,
+    Dirichlet walls on y, CFL 0.3, half-step initial velocity, `steps` steps."""
+    return Workload("plane128_nn_dd", (128, 128), (("N", "N"), ("D", "D")), 0.3, steps)
+
+
+def sno_initial_pressures(n: int, seed: int, ncells=(128, 128), sigma_cells=(9.0, 12.0),
+                          nblobs=(1, 3), dx=DX) -> np.ndarray:
+    """n initial pressures on the full node lattice, shape (n, N0+1, N1+1), FP64.
+
+    Each is 1 to 3 Gaussian blobs (count uniform in `nblobs`) of one width
+    sigma ~ U[9, 12] cells and amplitudes ~ U[-1, 1], centres uniform in
+    [4 sigma, L - 4 sigma]: smooth fields whose content beyond the 16th mode
+    of each axis is below 1e-2 of their peak.
+    """
+    rng = np.random.default_rng(seed)
+    out = np.zeros((n,) + tuple(k + 1 for k in ncells))
+    for s in range(n):
+        nb = int(rng.integers(nblobs[0], nblobs[1] + 1))
+        sig = float(rng.uniform(*sigma_cells))
+        w = Workload("sample", tuple(ncells), (), 0.3, 0,
+                     random_blobs(ncells, nb, sig, (-1.0, 1.0), int(rng.integers(1 << 30)), dx), dx)
+        out[s] = w.p0_full()
+    return out

@@ -7,6 +7,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2005_00322_gb300 import _abi, build as _build
@@ -24,7 +25,7 @@ def lib():
 def declared_symbols():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(pstd_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(pstd_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_header_declarations_have_bindings():
@@ -112,3 +113,24 @@ def test_reflection_combos_match_oracle(lib):
             assert abs(wv - rw) < 1e-15
     _, w = reflection_combos((8,), 1e-4, [(0.0, 0.5)])
     assert w == [0.375, 0.125, 0.375, 0.125]
+
+
+@pytest.mark.parametrize("bc", [("N", "N"), ("N", "D"), ("D", "N"), ("D", "D")])
+def test_sno_basis_matches_oracle(lib, bc):
+    """pstd_sno_basis (host, from the mode functions) equals the truncated T1
+    pair the oracle builds from the transform matrices of Table 2."""
+    from oracle import sno as osno
+    code = {"N": _abi.NEUMANN, "D": _abi.DIRICHLET}
+    N, K = 37, 12
+    T_ref, I_ref = osno.basis(N, bc, K)
+    lp = T_ref.shape[1]
+    T = (ctypes.c_float * (K * lp))()
+    I = (ctypes.c_float * (lp * K))()
+    assert lib.pstd_sno_basis(N, code[bc[0]], code[bc[1]], K, T, I) == 0
+    T = np.frombuffer(T, dtype=np.float32).reshape(K, lp)
+    I = np.frombuffer(I, dtype=np.float32).reshape(lp, K)
+    np.testing.assert_allclose(T, T_ref, atol=2e-6)
+    np.testing.assert_allclose(I, I_ref, atol=2e-7)
+    assert lib.pstd_sno_basis(N, code[bc[0]], code[bc[1]], lp + 1, T.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                              I.ctypes.data_as(ctypes.POINTER(ctypes.c_float))) == -1
+    assert lib.pstd_sno_basis(N, _abi.PERIODIC, _abi.PERIODIC, K, None, None) == -1
