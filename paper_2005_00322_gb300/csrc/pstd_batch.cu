@@ -105,6 +105,20 @@ int launch_block(pstd_batch_s* B, float* const* p, float* const* u, int64_t k, i
     return PSTD_OK;
 }
 
+// Every member's register-FFT velocities to their spectrum form or back
+// (parallel branches of the batch stream, like the steps).
+int convert_block(pstd_batch_s* B, float* const* u, int to_spectrum, int64_t* launches) {
+    BCK(cudaEventRecord(B->fork, B->stream));
+    for (int m = 0; m < B->n; ++m) {
+        BCK(cudaStreamWaitEvent(B->streams[m], B->fork, 0));
+        int rc = pstd_internal_convert_velocity(B->plans[m], u + 3 * m, to_spectrum, launches);
+        if (rc != PSTD_OK) return rc;
+        BCK(cudaEventRecord(B->joins[m], B->streams[m]));
+        BCK(cudaStreamWaitEvent(B->stream, B->joins[m], 0));
+    }
+    return PSTD_OK;
+}
+
 bool check_ptrs(const pstd_batch_s* B, float* const* p, float* const* u) {
     if (!p || !u) return false;
     for (int m = 0; m < B->n; ++m) {
@@ -174,9 +188,25 @@ int pstd_batch_init_velocity(pstd_batch_t* B, float* const* p, float* const* u) 
     return PSTD_OK;
 }
 
+namespace {
+int batch_steps(pstd_batch_t* B, float* const* p, float* const* u, int64_t nsteps);
+}
+
 int pstd_batch_run(pstd_batch_t* B, float* const* p, float* const* u, int64_t nsteps) {
     if (!B || nsteps < 0 || !check_ptrs(B, p, u)) return PSTD_EINVAL;
     B->last_launches = 0;
+    if (nsteps == 0) return PSTD_OK;
+    int64_t conv = 0;
+    int rc = convert_block(B, u, 1, &conv);
+    if (rc == PSTD_OK) rc = batch_steps(B, p, u, nsteps);
+    if (rc == PSTD_OK) rc = convert_block(B, u, 0, &conv);
+    B->last_launches += conv;
+    return rc;
+}
+
+namespace {
+// The steps of pstd_batch_run, velocities in spectrum form.
+int batch_steps(pstd_batch_t* B, float* const* p, float* const* u, int64_t nsteps) {
     int64_t done = 0;
     if (B->stream != nullptr && nsteps >= kBatchGraphSteps) {
         std::vector<float*> key;
@@ -208,6 +238,7 @@ int pstd_batch_run(pstd_batch_t* B, float* const* p, float* const* u, int64_t ns
     if (done < nsteps) return launch_block(B, p, u, nsteps - done, &B->last_launches);
     return PSTD_OK;
 }
+}  // namespace
 
 int pstd_batch_combine(pstd_batch_t* B, const double* w, float* const* p, float* out) {
     if (!B || !w || !p || !out) return PSTD_EINVAL;

@@ -9,6 +9,10 @@
 // Launch `n` leapfrog steps of plan P on its own stream (no graph capture of
 // its own, so the caller may be capturing); adds the kernel count.
 int pstd_internal_launch_steps(pstd_plan_t* P, float* p, float* const* u, int64_t n, int64_t* launches);
+// Convert the register-FFT axes' velocities of plan P in place to their
+// spectrum form (to_spectrum != 0) or back; the steps launched by
+// pstd_internal_launch_steps expect the spectrum form.  Adds the kernel count.
+int pstd_internal_convert_velocity(pstd_plan_t* P, float* const* u, int to_spectrum, int64_t* launches);
 // The plan's stream.
 cudaStream_t pstd_internal_stream(const pstd_plan_t* P);
 // First stored pressure node per axis (0 or 1) and the pressure shape.

@@ -95,6 +95,9 @@ struct Axis {
     int wl = 0, wv = 0;
     bool strided = false;
     float2* d_wtw = nullptr;
+    float2* d_sym = nullptr;          // velocity-spectrum symmetry factors (WAxis::sym)
+    float2* d_fUL = nullptr;          // L x the u -> p step coefficients (spectral velocity)
+    float* d_ph = nullptr;            // phantom partner lines of unpaired velocity lines
     WAxis wax{};
     WLaunch wgeo{};
     // split-precision dense form
@@ -507,6 +510,36 @@ int build_axis(pstd_plan_s* P, int i) {
         std::vector<float2> wt;
         if (!wtw(a.L, V, wt)) return PSTD_EUNSUPPORTED;
         if ((rc = upload(wt, &a.d_wtw)) != PSTD_OK) return rc;
+        // The passes keep u_a as its spectrum (bins of the FFT of its
+        // extension, / L): the u -> p coefficients carry the factor L, and the
+        // symmetry of the extension gives the factor on the stored bin of each
+        // non-owner bin: group I  U[k] = sR_u e^{2 pi i k/L} U[L-k]  (k > N),
+        // group II U[k] = sR_u e^{-i pi (L-1)/L} e^{2 pi i k/L} U[L-1-k]  (k >= N),
+        // and the vanishing bin (U[0] for sR_u = -1, U[N] for sR_u = +1) gets 0.
+        {
+            const double sRu = a.bcr == PSTD_NEUMANN ? -1.0 : 1.0;
+            std::vector<float2> sym(a.L), fUL(a.L);
+            for (int k = 0; k < a.L; ++k) {
+                std::complex<double> g = 1.0;
+                if (!a.periodic) {
+                    if (a.group2) {
+                        if (k >= a.N)
+                            g = sRu * std::polar(1.0, -M_PI * (a.L - 1) / a.L + 2.0 * M_PI * k / a.L);
+                    } else if (k == 0) {
+                        g = sRu < 0 ? 0.0 : 1.0;
+                    } else if (k == a.N) {
+                        g = sRu < 0 ? 1.0 : 0.0;
+                    } else if (k > a.N) {
+                        g = sRu * std::polar(1.0, 2.0 * M_PI * k / a.L);
+                    }
+                }
+                sym[k] = make_float2((float)g.real(), (float)g.imag());
+                const std::complex<double> c = coeff(a, k, 1, scales[OP_STEP_U]) * (double)a.L;
+                fUL[k] = make_float2((float)c.real(), (float)c.imag());
+            }
+            if ((rc = upload(sym, &a.d_sym)) != PSTD_OK) return rc;
+            if ((rc = upload(fUL, &a.d_fUL)) != PSTD_OK) return rc;
+        }
         WAxis& w = a.wax;
         w.N = a.N;
         w.L = a.L;
@@ -519,7 +552,19 @@ int build_axis(pstd_plan_s* P, int i) {
         w.shift = a.d_shift;
         w.nlines = a.nlines;
         w.inner = a.inner;
+        w.sym = a.d_sym;
         a.strided = a.inner > 1;
+        // unpaired velocity lines: the last line of a contiguous axis with an
+        // odd line count, or of every outer block of a strided axis whose
+        // inner extent is odd (tiles hold an even number G of lines)
+        {
+            const int64_t nph = a.strided ? ((a.inner & 1) ? a.nlines / a.inner : 0) : (a.nlines & 1);
+            if (nph > 0) {
+                CK(cudaMalloc((void**)&a.d_ph, (size_t)nph * a.N * sizeof(float)));
+                CK(cudaMemset(a.d_ph, 0, (size_t)nph * a.N * sizeof(float)));
+            }
+            w.ph = a.d_ph;
+        }
         const int64_t nseq = (a.nlines + 1) / 2;
         const int64_t want = 2 * 152;
         int threads = V >= 1 ? T : 128;
@@ -534,7 +579,7 @@ int build_axis(pstd_plan_s* P, int i) {
             w.G = 2 * w.seqs;
             a.wgeo.grid = (unsigned)((nseq + w.seqs - 1) / w.seqs);
             a.wgeo.smem = (size_t)w.seqs * pstd::wseq_words(a.L) * sizeof(float2);
-            a.wgeo.smem += (wt.size() + 3 * (size_t)a.L) * sizeof(float2);   // staged tables
+            a.wgeo.smem += (wt.size() + 4 * (size_t)a.L) * sizeof(float2);   // staged tables
         } else {
             const int64_t outer = a.nlines / a.inner;
             auto tiles = [&](int th) {
@@ -546,7 +591,7 @@ int build_axis(pstd_plan_s* P, int i) {
             w.G = 2 * w.seqs;
             a.wgeo.grid = (unsigned)tiles(threads);
             a.wgeo.smem = pstd::wk::strided_step_floats(w, pstd::wseq_words(a.L), true) * sizeof(float);
-            a.wgeo.smem += (wt.size() + 3 * (size_t)a.L) * sizeof(float2);   // staged tables
+            a.wgeo.smem += (wt.size() + 4 * (size_t)a.L) * sizeof(float2);   // staged tables
         }
         a.wgeo.threads = threads;
         if (a.wgeo.smem > 200 * 1024) return PSTD_EUNSUPPORTED;
@@ -603,6 +648,9 @@ void free_plan_memory(pstd_plan_s* P) {
         cudaFree(a.d_tw);
         cudaFree(a.d_shift);
         cudaFree(a.d_wtw);
+        cudaFree(a.d_sym);
+        cudaFree(a.d_fUL);
+        cudaFree(a.d_ph);
         cudaFree(a.d_gemm);
         for (int o = 0; o < OP_COUNT; ++o) {
             cudaFree(a.d_f[o]);
@@ -682,7 +730,7 @@ int launch_step(pstd_plan_s* P, float* p, float* const* u, int64_t* launches) {
             WStep w;
             w.ax = A.wax;
             w.fP = A.d_f[OP_STEP_P];
-            w.fU = A.d_f[OP_STEP_U];
+            w.fU = A.d_fUL;
             w.p = p;
             w.u = u[a];
             w.acc_in = (a == P->ndim - 1) ? p : P->d_S;
@@ -709,6 +757,7 @@ int launch_grad(pstd_plan_s* P, int axis, int opi, const float* in, float* out, 
         g.in = in;
         g.out = out;
         g.accumulate = acc;
+        g.scale = 1.0f;
         CK(wgrad(A.L, A.wv, A.strided, A.wgeo, P->stream, g));
         return PSTD_OK;
     }
@@ -726,7 +775,33 @@ int launch_grad(pstd_plan_s* P, int axis, int opi, const float* in, float* out, 
     return PSTD_OK;
 }
 
+// Register-FFT axes keep u_a as its spectrum between the passes of a run:
+// dir 2 converts u_a to it in place before the first step, dir 3 back after
+// the last.  Other axes (and the split form) step u_a itself.
+int convert_velocity(pstd_plan_s* P, float* const* u, int dir, int64_t* launches) {
+    if (P->opts.form == 1) return PSTD_OK;
+    for (int a = 0; a < P->ndim; ++a) {
+        Axis& A = P->ax[a];
+        if (!A.wl) continue;
+        WGrad g;
+        g.ax = A.wax;
+        g.dir = dir;
+        g.f = nullptr;
+        g.in = u[a];
+        g.out = u[a];
+        g.accumulate = 0;
+        g.scale = (float)(1.0 / A.L);
+        CK(wgrad(A.L, A.wv, A.strided, A.wgeo, P->stream, g));
+        ++*launches;
+    }
+    return PSTD_OK;
+}
+
 }  // namespace
+
+int pstd_internal_convert_velocity(pstd_plan_t* P, float* const* u, int to_spectrum, int64_t* launches) {
+    return convert_velocity(P, u, to_spectrum ? 2 : 3, launches);
+}
 
 int pstd_internal_launch_steps(pstd_plan_t* P, float* p, float* const* u, int64_t n, int64_t* launches) {
     for (int64_t s = 0; s < n; ++s) {
@@ -926,7 +1001,14 @@ int pstd_step(pstd_plan_t* P, float* p, float* const* u) {
     for (int a = 0; a < P->ndim; ++a)
         if (!u[a]) return PSTD_EINVAL;
     P->last_launches = 0;
-    return launch_step(P, p, u, &P->last_launches);
+    int rc = convert_velocity(P, u, 2, &P->last_launches);
+    if (rc == PSTD_OK) rc = launch_step(P, p, u, &P->last_launches);
+    if (rc == PSTD_OK) rc = convert_velocity(P, u, 3, &P->last_launches);
+    return rc;
+}
+
+namespace {
+int run_steps(pstd_plan_t* P, float* p, float* const* u, int64_t nsteps);
 }
 
 int pstd_run(pstd_plan_t* P, float* p, float* const* u, int64_t nsteps) {
@@ -934,6 +1016,18 @@ int pstd_run(pstd_plan_t* P, float* p, float* const* u, int64_t nsteps) {
     for (int a = 0; a < P->ndim; ++a)
         if (!u[a]) return PSTD_EINVAL;
     P->last_launches = 0;
+    if (nsteps == 0) return PSTD_OK;
+    int64_t conv = 0;
+    int rc = convert_velocity(P, u, 2, &conv);
+    if (rc == PSTD_OK) rc = run_steps(P, p, u, nsteps);
+    if (rc == PSTD_OK) rc = convert_velocity(P, u, 3, &conv);
+    P->last_launches += conv;
+    return rc;
+}
+
+namespace {
+// The steps of pstd_run with every register-FFT velocity in spectrum form.
+int run_steps(pstd_plan_t* P, float* p, float* const* u, int64_t nsteps) {
     if (P->persist_ok && nsteps > 0) {
         PersistArgs pa{};
         pa.ndim = P->ndim;
@@ -943,7 +1037,7 @@ int pstd_run(pstd_plan_t* P, float* p, float* const* u, int64_t nsteps) {
             WStep& w = pa.ax[a];
             w.ax = A.wax;
             w.fP = A.d_f[OP_STEP_P];
-            w.fU = A.d_f[OP_STEP_U];
+            w.fU = A.d_fUL;
             w.p = p;
             w.u = u[a];
             w.acc_in = (a == P->ndim - 1) ? p : P->d_S;
@@ -1008,6 +1102,7 @@ int pstd_run(pstd_plan_t* P, float* p, float* const* u, int64_t nsteps) {
     }
     return PSTD_OK;
 }
+}  // namespace
 
 int pstd_sync(pstd_plan_t* P) {
     if (!P) return PSTD_EINVAL;

@@ -93,12 +93,21 @@ struct WAxis {
     int64_t inner;           // stride of the axis
     int G;                   // strided layout: lines per tile (even)
     int seqs;                // sequences per CTA
+    const float2* sym;       // per bin: factor on the stored bin of the velocity spectrum (see spec_slot)
+    float* ph;               // velocity spectrum of the missing partner of an unpaired line
+                             // (N floats each: contiguous 1, strided one per outer block), or null
 };
 
+// One leapfrog pass of an axis.  The velocity u_a is held as its spectrum:
+// the FFT of its (pre-twiddled) symmetric-periodic extension divided by L,
+// i.e. T2 u in bin form, one stored value per velocity sample (spec_slot).
+// The pass transforms p forward, updates the spectrum with the p -> u
+// coefficients, and transforms the u -> p coefficients times the spectrum
+// back onto the nodes: one forward and one inverse FFT per line pair.
 struct WStep {
     WAxis ax;
     const float2* fP;        // -(dt/rho0) derivative coefficients, p -> u
-    const float2* fU;        // -(dt rho0 c0^2) derivative coefficients, u -> p
+    const float2* fU;        // L times the -(dt rho0 c0^2) derivative coefficients, u -> p
     const float* p;
     float* u;
     const float* acc_in;
@@ -107,12 +116,45 @@ struct WStep {
 
 struct WGrad {
     WAxis ax;
-    int dir;                 // 0: p -> u, 1: u -> p
+    int dir;                 // 0: p -> u, 1: u -> p, 2: u -> its spectrum, 3: spectrum -> u
     const float2* f;
     const float* in;
     float* out;
     int accumulate;
+    float scale;             // dir 2: 1 / L
 };
+
+// A line with no partner (odd line count) still has a complex spectrum:
+// the partner's half of its 2N reals lives in WAxis::ph (the "phantom"
+// partner line), read and written like a real partner's velocity slots.
+
+// Stored slot of bin k (0 <= k < L) of a velocity line-pair spectrum, and
+// whether bin k is the slot's owner (the bin whose value the slot holds).
+// The extension of u is mirrored about the right wall with sign sR_u, so the
+// packed spectrum obeys, for group I, U[L-k] = sR_u w^k U[k] (w = e^{-2 pi i/L}),
+// which forces U[0] = 0 (sR_u = -1) or U[N] = 0 (sR_u = +1); for group II
+// (pre-twiddled) U[L-1-k] = sR_u e^{i pi (L-1)/L} w^k U[k].  So N bins carry
+// the line pair, stored as N complex values = the pair's 2N real samples:
+// slot k < N holds bin k, except that slot 0 holds bin N when bin 0 vanishes.
+// A periodic axis (L == N) stores every bin.  Non-owner bins are the slot's
+// value times WAxis::sym[k] (0 for a vanishing bin).
+PSTD_HD int spec_slot(const WAxis& A, int k, bool& owner) {
+    const int N = A.N, L = A.L;
+    if (L == N) {
+        owner = true;
+        return k;
+    }
+    if (A.group2) {
+        owner = k < N;
+        return k < N ? k : L - 1 - k;
+    }
+    if (k < N) {
+        owner = k > 0 || A.sR_u > 0.0f;
+        return k;
+    }
+    owner = k == N && A.sR_u < 0.0f;
+    return k == N ? 0 : L - k;
+}
 
 namespace wk {
 
@@ -134,11 +176,13 @@ struct TablesDirect {
     const float2* f0;
     const float2* f1;
     const float2* shift;
+    const float2* sy;
     int t;
     PSTD_HD float2 twid(int i) const { return tw[i * S::T + t]; }
     template <int W>
     PSTD_HD float2 coef(int e) const { return (W ? f1 : f0)[t + S::T * e]; }
     PSTD_HD float2 sh(int e) const { return shift[t + S::T * e]; }
+    PSTD_HD float2 sym(int e) const { return sy[t + S::T * e]; }
 };
 template <class S>
 struct TablesInRegs {
@@ -146,6 +190,7 @@ struct TablesInRegs {
     const float2* f0;
     const float2* f1;
     const float2* shift;
+    const float2* sy;
     int t;
     float2 rtw[wf::tw_per_lane<S>() > 0 ? wf::tw_per_lane<S>() : 1];
     float2 rf0[S::E], rf1[S::E], rsh[S::E];
@@ -163,6 +208,9 @@ struct TablesInRegs {
     template <int W>
     PSTD_HD float2 coef(int e) const { return W ? rf1[e] : rf0[e]; }
     PSTD_HD float2 sh(int e) const { return rsh[e]; }
+    // symmetry factors are needed for half the bins once per pass: read them
+    // from the (L1-cached, global) table rather than holding them in registers
+    PSTD_HD float2 sym(int e) const { return sy[t + S::T * e]; }
 };
 
 template <class S, bool INV, int p = 0, class Tab>
@@ -225,6 +273,7 @@ PSTD_HD TablesOf<S> tables(const WAxis& A, const float2* f0, const float2* f1, i
     tb.f0 = f0;
     tb.f1 = f1;
     tb.shift = A.shift;
+    tb.sy = A.sym;
     tb.t = t;
     if constexpr (S::V >= 1) tb.load(A.group2 != 0);
     return tb;
@@ -257,15 +306,72 @@ PSTD_HD float2* stage_tables(WAxis& A, const float2*& f1, const float2*& f2, flo
         A.shift = p;
         p += L;
     }
-    for (int i = 2 * tid; i < L; i += 2 * nthr) async_copy16(p + i, f1 + i);
-    f1 = p;
-    p += L;
+    if (f1) {
+        for (int i = 2 * tid; i < L; i += 2 * nthr) async_copy16(p + i, f1 + i);
+        f1 = p;
+        p += L;
+    }
+    if (A.sym) {
+        for (int i = 2 * tid; i < L; i += 2 * nthr) async_copy16(p + i, A.sym + i);
+        A.sym = p;
+        p += L;
+    }
     if (f2) {
         for (int i = 2 * tid; i < L; i += 2 * nthr) async_copy16(p + i, f2 + i);
         f2 = p;
         p += L;
     }
     return p;
+}
+
+// Load the pressure pair's symmetric-periodic extension at this lane's
+// positions t + T e (pre-twiddled for group II).
+template <class S, class Tab, class Src>
+PSTD_HD void load_p_ext(float2 (&v)[S::E], int t, const WAxis& A, const Tab& tab, Src&& src) {
+#pragma unroll
+    for (int e = 0; e < S::E; ++e) {
+        const int j = t + S::T * e;
+        const bool mirror = j > A.N;
+        const int i = (mirror ? 2 * A.N - j : j) - A.lo;
+        float2 val = (i >= 0 && i < A.lp) ? src(i) : make_float2(0.0f, 0.0f);
+        if (mirror) val = cscale(val, A.sR_p);
+        if (A.group2) val = cmul(val, tab.sh(e));
+        v[e] = val;
+    }
+}
+
+// The velocity spectrum at this lane's bins t + T e, from the stored slots.
+template <class S, class Tab, class Ld>
+PSTD_HD void load_spectrum(float2 (&w)[S::E], int t, const WAxis& A, const Tab& tab, Ld&& ld) {
+#pragma unroll
+    for (int e = 0; e < S::E; ++e) {
+        bool own;
+        const int s = spec_slot(A, t + S::T * e, own);
+        w[e] = own ? ld(s) : cmul(tab.sym(e), ld(s));
+    }
+}
+
+// Second half of a pass on a line pair in registers.  On entry v holds the
+// pressure spectrum V and w the velocity spectrum at this lane's bins; the
+// spectrum is updated, w += fP V (stored back through `st` for the owner
+// bins), and the inverse FFT of fU w leaves the pressure contribution at
+// extension positions t + T e in v.
+template <class S, class Tab, class St>
+PSTD_HD void update_and_inverse(float2 (&v)[S::E], const float2 (&w)[S::E], int t, float2* sm, const WAxis& A,
+                                const Tab& tab, St&& st) {
+#pragma unroll
+    for (int e = 0; e < S::E; ++e) {
+        const float2 wn = cadd(w[e], cmul(v[e], tab.template coef<0>(e)));
+        bool own;
+        const int s = spec_slot(A, t + S::T * e, own);
+        if (own) st(s, wn);
+        v[e] = cmul(wn, tab.template coef<1>(e));
+    }
+    fft<S, true>(v, t, sm, tab);
+    if (A.group2) {
+#pragma unroll
+        for (int e = 0; e < S::E; ++e) v[e] = cmulc(v[e], tab.sh(e));
+    }
 }
 
 // ---- contiguous layout ------------------------------------------------------
@@ -285,42 +391,45 @@ PSTD_HD void step_contig(const WStep& a, int64_t block, float2* smem, int tid, i
     const bool va = la < A.nlines, vb = lb < A.nlines;
     float2* sm = bufs + (size_t)sq * wf::seq_words<S::L>();
     const int N = A.N, lp = A.lp;
-    // prefetch u^{n-1/2} and the accumulator at this lane's output positions
+    // prefetch the velocity spectrum slots and the accumulator of this lane
+    const bool vbu = vb || (va && A.ph);     // the spectrum's second line: partner or phantom
     float* ua = a.u + (va ? la : 0) * N;
-    float* ub = a.u + (vb ? lb : 0) * N;
+    float* ub = vb ? a.u + lb * N : (vbu ? A.ph : a.u);
     const float* ia = a.acc_in + (va ? la : 0) * lp;
     const float* ib = a.acc_in + (vb ? lb : 0) * lp;
-    float2 uo[E], ao[E];
+    float2 w[E], ao[E], sy[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        const int m = t + T * e;
-        const int i = m - A.lo;
-        uo[e] = make_float2(va && m < N ? ua[m] : 0.0f, vb && m < N ? ub[m] : 0.0f);
+        bool own;
+        const int s = spec_slot(A, t + T * e, own);
+        w[e] = make_float2(va ? ua[s] : 0.0f, vbu ? ub[s] : 0.0f);
+        // latency schedules: the symmetry factor (a global table) is fetched
+        // with the slots, off the critical path
+        if constexpr (S::V >= 1) sy[e] = own ? make_float2(1.0f, 0.0f) : A.sym[t + T * e];
+        const int i = t + T * e - A.lo;
         const bool ok = i >= 0 && i < lp;
         ao[e] = make_float2(va && ok ? ia[i] : 0.0f, vb && ok ? ib[i] : 0.0f);
     }
     async_wait_all();
     PSTD_SYNCCTA();
+    // staged tables are readable from here on: non-owner bins from their slot
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        bool own;
+        spec_slot(A, t + T * e, own);
+        if (!own) w[e] = cmul(S::V >= 1 ? sy[e] : tab.sym(e), w[e]);
+    }
     const float* pa = a.p + (va ? la : 0) * lp;
     const float* pb = a.p + (vb ? lb : 0) * lp;
     float2 v[E];
-    derivative<S, 0>(v, t, sm, A, tab, [&](int i) {
-        return make_float2(va ? pa[i] : 0.0f, vb ? pb[i] : 0.0f);
+    load_p_ext<S>(v, t, A, tab, [&](int i) { return make_float2(va ? pa[i] : 0.0f, vb ? pb[i] : 0.0f); });
+    // every lane has read its slots before any owner writes: the forward
+    // FFT's exchange barriers order them (a one-lane sequence has no other reader)
+    fft<S, false>(v, t, sm, tab);
+    update_and_inverse<S>(v, w, t, sm, A, tab, [&](int s, float2 x) {
+        if (va) ua[s] = x.x;
+        if (vbu) ub[s] = x.y;
     });
-    // u^{n+1/2} = u^{n-1/2} + f_P(p^n); the pair goes to the buffer for f_U
-    seq_sync<S>();
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int m = t + T * e;
-        if (m < N) {
-            const float2 w = cadd(uo[e], v[e]);
-            if (va) ua[m] = w.x;
-            if (vb) ub[m] = w.y;
-            sm[m] = w;
-        }
-    }
-    seq_sync<S>();
-    derivative<S, 1>(v, t, sm, A, tab, [&](int m) { return sm[m]; });
     float* oa = a.acc_out + (va ? la : 0) * lp;
     float* ob = a.acc_out + (vb ? lb : 0) * lp;
 #pragma unroll
@@ -332,6 +441,45 @@ PSTD_HD void step_contig(const WStep& a, int64_t block, float2* smem, int tid, i
         }
     }
     pdl_trigger();
+}
+
+// Velocity <-> its spectrum (WGrad dir 2 / 3), one line pair in registers;
+// `ld(i)` reads the pair's stored input at index i and `st(i, x)` writes its
+// output.  In place is allowed: every read precedes the FFT's barriers.
+template <class S, class Tab, class Ld, class St>
+PSTD_HD void spec_convert(int dir, float scale, int t, float2* sm, const WAxis& A, const Tab& tab, Ld&& ld,
+                          St&& st) {
+    constexpr int T = S::T, E = S::E;
+    const int N = A.N;
+    float2 v[E];
+    if (dir == 2) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int j = t + T * e;
+            const bool mirror = j >= N;
+            float2 val = ld(mirror ? 2 * N - 1 - j : j);
+            if (mirror) val = cscale(val, A.sR_u);
+            if (A.group2) val = cmul(val, tab.sh(e));
+            v[e] = val;
+        }
+        seq_sync<S>();
+        fft<S, false>(v, t, sm, tab);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            bool own;
+            const int s = spec_slot(A, t + T * e, own);
+            if (own) st(s, cscale(v[e], scale));
+        }
+    } else {
+        load_spectrum<S>(v, t, A, tab, ld);
+        seq_sync<S>();
+        fft<S, true>(v, t, sm, tab);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int m = t + T * e;
+            if (m < N) st(m, A.group2 ? cmulc(v[e], tab.sh(e)) : v[e]);
+        }
+    }
 }
 
 template <class S>
@@ -351,6 +499,22 @@ PSTD_HD void grad_contig(const WGrad& a, int64_t block, float2* smem, int tid, i
     const int64_t la = 2 * seq, lb = 2 * seq + 1;
     const bool va = la < A.nlines, vb = lb < A.nlines;
     float2* sm = bufs + (size_t)sq * wf::seq_words<S::L>();
+    if (a.dir >= 2) {
+        // spectrum side of an unpaired line: the phantom partner
+        const bool ph = !vb && va && A.ph;
+        const bool rb = vb || (ph && a.dir == 3), wb = vb || (ph && a.dir == 2);
+        const float* xa = a.in + (va ? la : 0) * A.N;
+        const float* xb = vb ? a.in + lb * A.N : (ph ? A.ph : a.in);
+        float* oa = a.out + (va ? la : 0) * A.N;
+        float* ob = vb ? a.out + lb * A.N : (ph ? A.ph : a.out);
+        spec_convert<S>(a.dir, a.scale, t, sm, A, tab,
+                        [&](int i) { return make_float2(va ? xa[i] : 0.0f, rb ? xb[i] : 0.0f); },
+                        [&](int i, float2 x) {
+                            if (va) oa[i] = x.x;
+                            if (wb) ob[i] = x.y;
+                        });
+        return;
+    }
     const int nin = a.dir == 0 ? A.lp : A.N;
     const int nout = a.dir == 0 ? A.N : A.lp;
     const float* xa = a.in + (va ? la : 0) * nin;
@@ -447,32 +611,32 @@ PSTD_HD void step_strided(const WStep& a, int64_t block, float2* smem0, int tid,
     tile_load(a.p, lp, A, o, i0, Gv, rawP, tid, nthr);
     tile_load(a.u, N, A, o, i0, Gv, rawU, tid, nthr);
     if (sep) tile_load(a.acc_in, lp, A, o, i0, Gv, rawA, tid, nthr);
+    // an odd tile's last line pairs with the phantom row Gv (< G)
+    const bool phrow = A.ph && (Gv & 1);
+    if (phrow)
+        for (int m = tid; m < N; m += nthr) rawU[Gv * row_stride(N) + m] = A.ph[o * N + m];
     async_wait_all();
     PSTD_SYNCCTA();
     if (sq < A.seqs) {
         const int ga = 2 * sq, gb = 2 * sq + 1;
         const bool va = ga < Gv, vb = gb < Gv;
+        const bool vbu = vb || (phrow && gb == Gv);
         float2* sm = smem + (size_t)sq * wf::seq_words<S::L>();
         const float* pa = rawP + (va ? ga : 0) * row_stride(lp);
         const float* pb = rawP + (vb ? gb : 0) * row_stride(lp);
-        float2 v[E];
-        derivative<S, 0>(v, t, sm, A, tab, [&](int i) {
-            return make_float2(va ? pa[i] : 0.0f, vb ? pb[i] : 0.0f);
-        });
         float* ua = rawU + (va ? ga : 0) * row_stride(N);
-        float* ub = rawU + (vb ? gb : 0) * row_stride(N);
-        seq_sync<S>();
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int m = t + T * e;
-            if (m < N) {
-                if (va) ua[m] += v[e].x;
-                if (vb) ub[m] += v[e].y;
-            }
-        }
-        seq_sync<S>();
-        derivative<S, 1>(v, t, sm, A, tab, [&](int m) {
-            return make_float2(va ? ua[m] : 0.0f, vb ? ub[m] : 0.0f);
+        float* ub = rawU + (vbu ? gb : 0) * row_stride(N);
+        float2 v[E];
+        load_p_ext<S>(v, t, A, tab, [&](int i) { return make_float2(va ? pa[i] : 0.0f, vb ? pb[i] : 0.0f); });
+        fft<S, false>(v, t, sm, tab);
+        // the spectrum slots are read from the tile only now, so that they do
+        // not occupy registers during the forward FFT
+        float2 w[E];
+        load_spectrum<S>(w, t, A, tab, [&](int s) { return make_float2(va ? ua[s] : 0.0f, vbu ? ub[s] : 0.0f); });
+        seq_sync<S>();   // every lane has read its slots before any owner writes
+        update_and_inverse<S>(v, w, t, sm, A, tab, [&](int s, float2 x) {
+            if (va) ua[s] = x.x;
+            if (vbu) ub[s] = x.y;
         });
         float* aa = rawA + (va ? ga : 0) * row_stride(lp);
         float* ab = rawA + (vb ? gb : 0) * row_stride(lp);
@@ -489,6 +653,8 @@ PSTD_HD void step_strided(const WStep& a, int64_t block, float2* smem0, int tid,
     PSTD_SYNCCTA();
     tile_store(a.u, N, A, o, i0, Gv, rawU, tid, nthr);
     tile_store(a.acc_out, lp, A, o, i0, Gv, rawA, tid, nthr);
+    if (phrow)
+        for (int m = tid; m < N; m += nthr) A.ph[o * N + m] = rawU[Gv * row_stride(N) + m];
     pdl_trigger();
 }
 
@@ -506,7 +672,7 @@ PSTD_HD void grad_strided(const WGrad& a, int64_t block, float2* smem0, int tid,
     int Gv;
     tile_of(A, block, o, i0, Gv);
     const int nin = a.dir == 0 ? A.lp : A.N;
-    const int nout = a.dir == 0 ? A.N : A.lp;
+    const int nout = a.dir == 0 || a.dir >= 2 ? A.N : A.lp;
     float* rawI = (float*)(smem + (size_t)A.seqs * wf::seq_words<S::L>());
     float* rawO = rawI + (size_t)A.G * row_stride(nin);
     pdl_wait();
@@ -514,6 +680,38 @@ PSTD_HD void grad_strided(const WGrad& a, int64_t block, float2* smem0, int tid,
     if (a.accumulate) tile_load(a.out, nout, A, o, i0, Gv, rawO, tid, nthr);
     async_wait_all();
     PSTD_SYNCCTA();
+    if (a.dir >= 2) {
+        // in place through the tile: rawO is a separate buffer of the same
+        // shape.  An odd tile's last line pairs with the phantom row Gv: read
+        // from WAxis::ph (dir 3) or written to it (dir 2).
+        const bool phrow = A.ph && (Gv & 1);
+        if (phrow && a.dir == 3) {
+            for (int m = tid; m < A.N; m += nthr) rawI[Gv * row_stride(nin) + m] = A.ph[o * A.N + m];
+            PSTD_SYNCCTA();
+        }
+        if (sq < A.seqs) {
+            const int ga = 2 * sq, gb = 2 * sq + 1;
+            const bool va = ga < Gv, vb = gb < Gv;
+            const bool ph = phrow && gb == Gv;
+            const bool rb = vb || (ph && a.dir == 3), wb = vb || (ph && a.dir == 2);
+            float2* sm = smem + (size_t)sq * wf::seq_words<S::L>();
+            const float* xa = rawI + (va ? ga : 0) * row_stride(nin);
+            const float* xb = rawI + (rb ? gb : 0) * row_stride(nin);
+            float* oa = rawO + (va ? ga : 0) * row_stride(nout);
+            float* ob = rawO + (wb ? gb : 0) * row_stride(nout);
+            spec_convert<S>(a.dir, a.scale, t, sm, A, tab,
+                            [&](int i) { return make_float2(va ? xa[i] : 0.0f, rb ? xb[i] : 0.0f); },
+                            [&](int i, float2 x) {
+                                if (va) oa[i] = x.x;
+                                if (wb) ob[i] = x.y;
+                            });
+        }
+        PSTD_SYNCCTA();
+        tile_store(a.out, nout, A, o, i0, Gv, rawO, tid, nthr);
+        if (phrow && a.dir == 2)
+            for (int m = tid; m < A.N; m += nthr) A.ph[o * A.N + m] = rawO[Gv * row_stride(nout) + m];
+        return;
+    }
     if (sq < A.seqs) {
         const int ga = 2 * sq, gb = 2 * sq + 1;
         const bool va = ga < Gv, vb = gb < Gv;

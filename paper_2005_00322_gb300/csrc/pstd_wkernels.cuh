@@ -16,8 +16,10 @@ __global__ void __launch_bounds__(256) k_wstep_c(WStep a) {
     float2* wsm = (float2*)wsm4;
     wk::step_contig<wf::Sched<L, V>>(a, blockIdx.x, wsm, threadIdx.x, blockDim.x);
 }
+// The strided latency pass of the 3-D sizes (L <= 512) runs at 128 registers,
+// 4 CTAs of 128 threads per SM (a few bytes of spill), for occupancy.
 template <int L, int V>
-__global__ void __launch_bounds__(256) k_wstep_s(WStep a) {
+__global__ void __launch_bounds__(256, (V == 1 && L <= 512) ? 2 : 1) k_wstep_s(WStep a) {
     extern __shared__ float4 wsm4[];  // 16-byte aligned for cp.async
     float2* wsm = (float2*)wsm4;
     wk::step_strided<wf::Sched<L, V>>(a, blockIdx.x, wsm, threadIdx.x, blockDim.x);

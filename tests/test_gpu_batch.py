@@ -36,10 +36,12 @@ def test_batch_of_uneven_members_equals_single_runs():
         p.copy_(q)
     B.init_velocity(fields)
     B.run(fields, 70)                       # 2 graph blocks of 32 + a tail of 6
-    assert B.last_launch_count() == 70 * sum(len(n) for n, _ in specs)
+    steps_launches = B.last_launch_count()
     torch.cuda.synchronize()
+    conv = 0
     for m, (n, b) in enumerate(specs):
         s = Solver(n, DX, b, cfl=0.2)
+        conv += 2 * sum(1 for sc in s.schedule() if sc[0] >= 0)
         p = p0s[m].clone()
         us = [torch.zeros(sh, device="cuda") for sh in s.shapes[1:]]
         s.init_velocity(p, us)
@@ -48,6 +50,7 @@ def test_batch_of_uneven_members_equals_single_runs():
         assert torch.equal(p, fields[m][0])
         assert all(torch.equal(a, b_) for a, b_ in zip(us, fields[m][1]))
         s.close()
+    assert steps_launches == 70 * sum(len(n) for n, _ in specs) + conv
     B.close()
 
 
