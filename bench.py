@@ -240,8 +240,7 @@ class SingleRunner:
             h.copy_(d, non_blocking=True)
 
     def leapfrog(self, n):
-        for _ in range(n):
-            self.solver.step(self.p, self.us)
+        self.solver.run(self.p, self.us, n)
 
     def close(self):
         self.solver.close()
@@ -487,16 +486,20 @@ def main():
     updates = run.cells * steps_per * args.steps * world
     value = whole_job_rate(run.cells * steps_per * args.steps, world, t)
 
-    # dominant kernel: the fused axis pass; mean duration per launch from
-    # events around direct (non-graph) leapfrog steps on the plan's stream
-    nk = 64 if single else 4
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    run.leapfrog(nk)
-    e1.record(st)
-    e1.synchronize()
-    step_s = e0.elapsed_time(e1) / 1e3 / nk
+    # dominant kernel: the fused axis pass.  Its mean duration inside a run
+    # comes from events on the plan's stream around two graph-replayed runs
+    # of 32 and 96 steps: the difference cancels the per-run velocity
+    # conversions and launch set-up, leaving 64 steps of axis passes.
+    def run_time(n):
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(st)
+        run.leapfrog(n)
+        a1.record(st)
+        a1.synchronize()
+        return a0.elapsed_time(a1) / 1e3
+    run_time(32)
+    step_s = (run_time(96) - run_time(32)) / 64
     alg_step = sum(2 * (len(m) + 1) * 4 * int(np.prod(m)) for m in
                    ([mm.ncells for mm in members_of(w)] if single or isinstance(w, list)
                     else [w.ncells] * len(run.weights)))
