@@ -378,6 +378,11 @@ PSTD_HD void update_and_inverse(float2 (&v)[S::E], const float2 (&w)[S::E], int 
 template <class S>
 PSTD_HD void step_contig(const WStep& a, int64_t block, float2* smem, int tid, int nthr) {
     constexpr int T = S::T, E = S::E;
+    // Lean form (the 3-D lengths): nothing is prefetched across the forward
+    // FFT, so that the pass fits 128 registers and 4 CTAs per SM; the 2-D
+    // length 1024 is latency-bound and prefetches the slots, the symmetry
+    // factors and the accumulator with the tables.
+    constexpr bool lean = S::V >= 1 && S::L <= 512;
     int sq, t;
     lane_of<S>(tid, sq, t);
     WAxis A = a.ax;
@@ -391,41 +396,53 @@ PSTD_HD void step_contig(const WStep& a, int64_t block, float2* smem, int tid, i
     const bool va = la < A.nlines, vb = lb < A.nlines;
     float2* sm = bufs + (size_t)sq * wf::seq_words<S::L>();
     const int N = A.N, lp = A.lp;
-    // prefetch the velocity spectrum slots and the accumulator of this lane
     const bool vbu = vb || (va && A.ph);     // the spectrum's second line: partner or phantom
     float* ua = a.u + (va ? la : 0) * N;
     float* ub = vb ? a.u + lb * N : (vbu ? A.ph : a.u);
     const float* ia = a.acc_in + (va ? la : 0) * lp;
     const float* ib = a.acc_in + (vb ? lb : 0) * lp;
-    float2 w[E], ao[E], sy[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        bool own;
-        const int s = spec_slot(A, t + T * e, own);
-        w[e] = make_float2(va ? ua[s] : 0.0f, vbu ? ub[s] : 0.0f);
-        // latency schedules: the symmetry factor (a global table) is fetched
-        // with the slots, off the critical path
-        if constexpr (S::V >= 1) sy[e] = own ? make_float2(1.0f, 0.0f) : A.sym[t + T * e];
+    auto slot = [&](int s) { return make_float2(va ? ua[s] : 0.0f, vbu ? ub[s] : 0.0f); };
+    auto acc = [&](int e) {
         const int i = t + T * e - A.lo;
         const bool ok = i >= 0 && i < lp;
-        ao[e] = make_float2(va && ok ? ia[i] : 0.0f, vb && ok ? ib[i] : 0.0f);
+        return make_float2(va && ok ? ia[i] : 0.0f, vb && ok ? ib[i] : 0.0f);
+    };
+    float2 w[E], ao[E], sy[E];
+    if constexpr (!lean) {
+        // prefetch this lane's spectrum slots and accumulator
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            bool own;
+            const int s = spec_slot(A, t + T * e, own);
+            w[e] = slot(s);
+            // latency schedules: the symmetry factor (a global table) is
+            // fetched with the slots, off the critical path
+            if constexpr (S::V >= 1) sy[e] = own ? make_float2(1.0f, 0.0f) : A.sym[t + T * e];
+            ao[e] = acc(e);
+        }
     }
     async_wait_all();
     PSTD_SYNCCTA();
-    // staged tables are readable from here on: non-owner bins from their slot
+    if constexpr (!lean) {
+        // staged tables are readable from here on: non-owner bins from their slot
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        bool own;
-        spec_slot(A, t + T * e, own);
-        if (!own) w[e] = cmul(S::V >= 1 ? sy[e] : tab.sym(e), w[e]);
+        for (int e = 0; e < E; ++e) {
+            bool own;
+            spec_slot(A, t + T * e, own);
+            if (!own) w[e] = cmul(S::V >= 1 ? sy[e] : tab.sym(e), w[e]);
+        }
     }
     const float* pa = a.p + (va ? la : 0) * lp;
     const float* pb = a.p + (vb ? lb : 0) * lp;
     float2 v[E];
     load_p_ext<S>(v, t, A, tab, [&](int i) { return make_float2(va ? pa[i] : 0.0f, vb ? pb[i] : 0.0f); });
-    // every lane has read its slots before any owner writes: the forward
-    // FFT's exchange barriers order them (a one-lane sequence has no other reader)
     fft<S, false>(v, t, sm, tab);
+    if constexpr (lean) {
+        load_spectrum<S>(w, t, A, tab, slot);
+        seq_sync<S>();   // every lane has read its slots before any owner writes
+    }
+    // (prefetched form: the forward FFT's exchange barriers ordered the reads
+    // before the owner writes; a one-lane sequence has no other reader)
     update_and_inverse<S>(v, w, t, sm, A, tab, [&](int s, float2 x) {
         if (va) ua[s] = x.x;
         if (vbu) ub[s] = x.y;
@@ -436,8 +453,9 @@ PSTD_HD void step_contig(const WStep& a, int64_t block, float2* smem, int tid, i
     for (int e = 0; e < E; ++e) {
         const int i = t + T * e - A.lo;
         if (i >= 0 && i < lp) {
-            if (va) oa[i] = ao[e].x + v[e].x;
-            if (vb) ob[i] = ao[e].y + v[e].y;
+            const float2 c = lean ? acc(e) : ao[e];
+            if (va) oa[i] = c.x + v[e].x;
+            if (vb) ob[i] = c.y + v[e].y;
         }
     }
     pdl_trigger();

@@ -10,8 +10,10 @@
 
 namespace pstd {
 
+// The contiguous latency pass of the 3-D sizes (L <= 512, the lean form of
+// step_contig) also runs at 128 registers.
 template <int L, int V>
-__global__ void __launch_bounds__(256) k_wstep_c(WStep a) {
+__global__ void __launch_bounds__(256, (V == 1 && L <= 512) ? 2 : 1) k_wstep_c(WStep a) {
     extern __shared__ float4 wsm4[];  // 16-byte aligned for cp.async
     float2* wsm = (float2*)wsm4;
     wk::step_contig<wf::Sched<L, V>>(a, blockIdx.x, wsm, threadIdx.x, blockDim.x);
