@@ -261,10 +261,17 @@ PSTD_HD void derivative(float2 (&v)[S::E], int t, float2* sm, const WAxis& A, co
     }
 }
 
+// Schedules whose lanes hold at most 8 elements keep their tables in
+// registers; the others stage them in shared memory.
+template <class S>
+constexpr bool reg_tables() {
+    return S::V >= 1 && S::E <= 8;
+}
+
 // Tables of one derivative for schedule S (registers for the latency
 // schedules, direct access otherwise).
 template <class S>
-using TablesOf = typename std::conditional<S::V >= 1, TablesInRegs<S>, TablesDirect<S>>::type;
+using TablesOf = typename std::conditional<reg_tables<S>(), TablesInRegs<S>, TablesDirect<S>>::type;
 
 template <class S>
 PSTD_HD TablesOf<S> tables(const WAxis& A, const float2* f0, const float2* f1, int t) {
@@ -275,7 +282,7 @@ PSTD_HD TablesOf<S> tables(const WAxis& A, const float2* f0, const float2* f1, i
     tb.shift = A.shift;
     tb.sy = A.sym;
     tb.t = t;
-    if constexpr (S::V >= 1) tb.load(A.group2 != 0);
+    if constexpr (reg_tables<S>()) tb.load(A.group2 != 0);
     return tb;
 }
 
@@ -294,7 +301,7 @@ PSTD_HD void lane_of(int tid, int& seq, int& t) {
 template <class S>
 PSTD_HD float2* stage_tables(WAxis& A, const float2*& f1, const float2*& f2, float2* dst, int tid,
                              int nthr) {
-    if constexpr (S::V >= 1) return dst;   // latency schedules keep tables in registers
+    if constexpr (reg_tables<S>()) return dst;   // these schedules keep tables in registers
     constexpr int ntw = (wf::tw_total<S>() + 1) & ~1;
     constexpr int L = S::L;
     float2* p = dst;
@@ -378,11 +385,11 @@ PSTD_HD void update_and_inverse(float2 (&v)[S::E], const float2 (&w)[S::E], int 
 template <class S>
 PSTD_HD void step_contig(const WStep& a, int64_t block, float2* smem, int tid, int nthr) {
     constexpr int T = S::T, E = S::E;
-    // Lean form (the 3-D lengths): nothing is prefetched across the forward
+    // Lean form (the 3-D lengths, L <= 768): nothing is prefetched across the forward
     // FFT, so that the pass fits 128 registers and 4 CTAs per SM; the 2-D
     // length 1024 is latency-bound and prefetches the slots, the symmetry
     // factors and the accumulator with the tables.
-    constexpr bool lean = S::V >= 1 && S::L <= 512;
+    constexpr bool lean = S::V >= 1 && S::L <= 768;
     int sq, t;
     lane_of<S>(tid, sq, t);
     WAxis A = a.ax;
@@ -417,7 +424,7 @@ PSTD_HD void step_contig(const WStep& a, int64_t block, float2* smem, int tid, i
             w[e] = slot(s);
             // latency schedules: the symmetry factor (a global table) is
             // fetched with the slots, off the critical path
-            if constexpr (S::V >= 1) sy[e] = own ? make_float2(1.0f, 0.0f) : A.sym[t + T * e];
+            if constexpr (reg_tables<S>()) sy[e] = own ? make_float2(1.0f, 0.0f) : A.sym[t + T * e];
             ao[e] = acc(e);
         }
     }
@@ -429,7 +436,7 @@ PSTD_HD void step_contig(const WStep& a, int64_t block, float2* smem, int tid, i
         for (int e = 0; e < E; ++e) {
             bool own;
             spec_slot(A, t + T * e, own);
-            if (!own) w[e] = cmul(S::V >= 1 ? sy[e] : tab.sym(e), w[e]);
+            if (!own) w[e] = cmul(reg_tables<S>() ? sy[e] : tab.sym(e), w[e]);
         }
     }
     const float* pa = a.p + (va ? la : 0) * lp;

@@ -10,18 +10,18 @@
 
 namespace pstd {
 
-// The contiguous latency pass of the 3-D sizes (L <= 512, the lean form of
+// The contiguous latency pass of the 3-D sizes (L <= 768, the lean form of
 // step_contig) also runs at 128 registers.
 template <int L, int V>
-__global__ void __launch_bounds__(256, (V == 1 && L <= 512) ? 2 : 1) k_wstep_c(WStep a) {
+__global__ void __launch_bounds__(256, (V == 1 && L <= 768) ? 2 : 1) k_wstep_c(WStep a) {
     extern __shared__ float4 wsm4[];  // 16-byte aligned for cp.async
     float2* wsm = (float2*)wsm4;
     wk::step_contig<wf::Sched<L, V>>(a, blockIdx.x, wsm, threadIdx.x, blockDim.x);
 }
-// The strided latency pass of the 3-D sizes (L <= 512) runs at 128 registers,
+// The strided latency pass of the 3-D sizes (L <= 768) runs at 128 registers,
 // 4 CTAs of 128 threads per SM (a few bytes of spill), for occupancy.
 template <int L, int V>
-__global__ void __launch_bounds__(256, (V == 1 && L <= 512) ? 2 : 1) k_wstep_s(WStep a) {
+__global__ void __launch_bounds__(256, (V == 1 && L <= 768) ? 2 : 1) k_wstep_s(WStep a) {
     extern __shared__ float4 wsm4[];  // 16-byte aligned for cp.async
     float2* wsm = (float2*)wsm4;
     wk::step_strided<wf::Sched<L, V>>(a, blockIdx.x, wsm, threadIdx.x, blockDim.x);
@@ -152,12 +152,15 @@ void wtwiddles(std::vector<float2>& out) {
 
 // Lanes per sequence of Sched<L, 2> (fewer, wider passes; 0: none).
 inline int wlanes_v2(int L) { return L == 1024 ? 64 : 0; }
+// Lanes per sequence of Sched<L, 3> (more lanes, 4 elements each; 0: none).
+inline int wlanes_v3(int L) { return L == 1024 ? 256 : 0; }
 
 // Lanes per sequence of the latency schedule Sched<L, 1> (0: none).
 inline int wlanes_latency(int L) {
     switch (L) {
         case 256: return 32;
         case 512: return 64;
+        case 768: return 64;
         case 1024: return 128;
         default: return 0;
     }
