@@ -102,8 +102,8 @@ int pstd_plan(const pstd_desc* desc, void* stream, pstd_plan_t** out);
  * plan.  variant 0 keeps many elements per lane and few FFT passes (for axes
  * with many lines), variant 1 spreads each FFT over up to 128 lanes (FFT
  * lengths 256, 512, 768, 1024), variant 2 (length 1024) uses 64 lanes of 16
- * elements, variant 3 (length 1024) 256 lanes of 4 elements (the default
- * for length-1024 axes with too few lines to fill the GPU).
+ * elements, variant 3 (lengths 512, 1024) 128 / 256 lanes of 4 elements (the
+ * default for those lengths on axes with too few lines to fill the GPU).
  * seqs_per_cta: line pairs per CTA (a power of two). */
 typedef struct {
     int variant[3];

@@ -508,9 +508,10 @@ int build_axis(pstd_plan_s* P, int i) {
         V = 1;
         T = pstd::wlanes_latency(a.L);
     }
-    // length-1024 axes with few lines (the 2-D sizes): 256 lanes of 4
-    // elements shorten each lane's dependent chain; measured 13.7 -> 12.2 us
-    // per 512^2 step
+    // length-512/1024 axes with few lines (the 2-D sizes): 128 / 256 lanes of
+    // 4 elements shorten each lane's dependent chain; measured 13.7 -> 12.2 us
+    // per 512^2 step and 14.2 -> 9.3 us per 256^2 step (with many lines, as
+    // in 256^3, the 8-element schedule stays faster: 0.69 vs 0.94 ms)
     if (ov < 0 && V == 1 && pstd::wlanes_v3(a.L) > 0 && (a.nlines + 1) / 2 < 2 * 2 * 152) {
         V = 3;
         T = pstd::wlanes_v3(a.L);

@@ -148,6 +148,7 @@ PSTD_SCHED(1024, 1, 128, 8, 8, 8, 2)
 PSTD_SCHED(1024, 2, 64, 16, 16, 4)
 PSTD_SCHED(768, 1, 64, 4, 4, 4, 4, 3)
 PSTD_SCHED(1024, 3, 256, 4, 4, 4, 4, 4)
+PSTD_SCHED(512, 3, 128, 4, 4, 4, 4, 2)
 #undef PSTD_SCHED
 
 // Ns before pass p (product of earlier radices)

@@ -153,7 +153,7 @@ void wtwiddles(std::vector<float2>& out) {
 // Lanes per sequence of Sched<L, 2> (fewer, wider passes; 0: none).
 inline int wlanes_v2(int L) { return L == 1024 ? 64 : 0; }
 // Lanes per sequence of Sched<L, 3> (more lanes, 4 elements each; 0: none).
-inline int wlanes_v3(int L) { return L == 1024 ? 256 : 0; }
+inline int wlanes_v3(int L) { return L == 1024 ? 256 : (L == 512 ? 128 : 0); }
 
 // Lanes per sequence of the latency schedule Sched<L, 1> (0: none).
 inline int wlanes_latency(int L) {
