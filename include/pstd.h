@@ -196,6 +196,39 @@ int64_t pstd_last_launch_count(const pstd_plan_t* plan);
 /* Library version string. */
 const char* pstd_version(void);
 
+/* ---- Plain differentiation and staggered interpolation (Section 3.3) ------- */
+/* Field kinds along one axis of a plan: the grid (nodes x_j = j dx or
+ * half-nodes (m + 1/2) dx) and the parity class at the walls.  Pressure-like
+ * fields are symmetric about a Neumann wall and antisymmetric about a
+ * Dirichlet wall, velocity-like fields the reverse; a node where a field is
+ * antisymmetric about a wall is zero and not stored.  PSTD_NODES_P is the
+ * layout of p and PSTD_HALF_U that of u_axis; PSTD_NODES_U holds e.g. dp/dx on
+ * the nodes (N+1 minus one per Neumann wall entries) and PSTD_HALF_P e.g. p
+ * interpolated to the half-nodes (N entries).  On a periodic axis every kind
+ * has N entries. */
+enum { PSTD_NODES_P = 0, PSTD_HALF_U = 1, PSTD_NODES_U = 2, PSTD_HALF_P = 3 };
+/* PSTD_OP_DIFF: spectral derivative on the same grid (Tables A1, A4); the
+ *   parity class swaps: NODES_P <-> NODES_U, HALF_U <-> HALF_P.
+ * PSTD_OP_INTERP: spectral interpolation to the other grid, half a cell
+ *   away (Tables A2, A5); the parity class stays: NODES_P <-> HALF_P,
+ *   NODES_U <-> HALF_U.
+ * (The staggered derivative of Tables A3 / A6 is pstd_grad.) */
+enum { PSTD_OP_DIFF = 0, PSTD_OP_INTERP = 1 };
+
+/* Shape of a field of `kind` along `axis` (the other axes as p).
+ * Errors: PSTD_EINVAL (bad axis or kind, or a kind with no stored node). */
+int pstd_apply_shape(const pstd_plan_t* plan, int axis, int kind, int64_t shape[3]);
+
+/* out = op(in) along `axis`, for a field `in` of `kind` (device pointers,
+ * layouts from pstd_apply_shape for `kind` and for the output kind above).
+ * The multiplier on the symmetric-periodic extension is i k (differentiation)
+ * or e^{+-i k dx/2} (interpolation), with only its real part kept at an even
+ * period's Nyquist bin; in exact arithmetic this is the paper's DTT pair of
+ * the field's symmetry with its drop / pad bookkeeping.  Tables are built in
+ * FP64 on first use of (axis, op, kind) and kept by the plan.
+ * Errors: PSTD_EINVAL, PSTD_ENOMEM, PSTD_ECUDA, PSTD_EUNSUPPORTED. */
+int pstd_apply(pstd_plan_t* plan, int axis, int op, int kind, const float* in, float* out);
+
 /* ---- Batched runs and reflection coefficients (Section 5) ------------------ */
 
 typedef struct pstd_batch_s pstd_batch_t;

@@ -10,6 +10,8 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libp
 
 NEUMANN, DIRICHLET, PERIODIC = 0, 1, 2
 U_HALFSTEP, U_AS_GIVEN = 0, 1
+NODES_P, HALF_U, NODES_U, HALF_P = 0, 1, 2, 3
+OP_DIFF, OP_INTERP = 0, 1
 
 ERRORS = {0: "PSTD_OK", -1: "PSTD_EINVAL", -2: "PSTD_EUNSTABLE", -3: "PSTD_ENOMEM",
           -4: "PSTD_ECUDA", -5: "PSTD_ETIMEOUT", -6: "PSTD_EUNSUPPORTED"}
@@ -23,6 +25,8 @@ SIGNATURES = {
     "pstd_field_shape": (c_int, [c_void_p, c_int, POINTER(c_int64)]),
     "pstd_field_numel": (c_int64, [c_void_p, c_int]),
     "pstd_grad": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
+    "pstd_apply_shape": (c_int, [c_void_p, c_int, c_int, POINTER(c_int64)]),
+    "pstd_apply": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
     "pstd_init_velocity": (c_int, [c_void_p, c_void_p, POINTER(c_void_p)]),
     "pstd_step": (c_int, [c_void_p, c_void_p, POINTER(c_void_p)]),
     "pstd_run": (c_int, [c_void_p, c_void_p, POINTER(c_void_p), c_int64]),

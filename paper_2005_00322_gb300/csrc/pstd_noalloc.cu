@@ -195,6 +195,8 @@ extern "C" int pstd_step_noalloc(const pstd_desc* d, float* p, float* const* u, 
             op.L = L;
             op.group2 = bcl != bcr;
             op.dir = dir;
+            op.in_half = dir;
+            op.out_half = 1 - dir;
             op.nin = dir == 0 ? lp : N;
             op.nout = dir == 0 ? N : lp;
             op.in_lo = lo;

@@ -60,11 +60,12 @@ struct LineOp {
     int L;                  // FFT length M = 2N
     int group2;             // 1: antiperiodic extension (ND, DN)
     int dir;                // 0: pressure nodes -> half-nodes, 1: half-nodes -> nodes
+    int in_half, out_half;  // grid of the input / output: 0 nodes, 1 half-nodes
     int nin, nout;          // stored input / output line lengths
-    int in_lo;              // dir 0: first stored node (0 or 1)
-    int out_lo;             // dir 1: first stored node (0 or 1)
-    float s_right;          // dir 0: wall sign of p at the right wall (+1 N, -1 D)
-                            // dir 1: wall sign of u at the right wall (-1 N, +1 D)
+    int in_lo;              // input on nodes: first stored node (0 or 1)
+    int out_lo;             // output on nodes: first stored node (0 or 1)
+    float s_right;          // sign of the input reflected about the right wall
+                            // (pressure-like on nodes: +1 N, -1 D; velocity: -1 N, +1 D)
     const float2* f;        // L folded coefficients (complex)
     const float2* shift;    // group II: exp(-i pi j / L), j < L
     const float* dense;     // kind 1: nout x nin row-major operator
@@ -219,15 +220,15 @@ PSTD_HD void phase_extend(const LineOp& op, const float* raw, int rs, int G, flo
         // position in the stored line and sign, or -1 for a zero
         int src;
         float sg;
-        if (op.dir == 0) {
-            // pressure on nodes: node q in [0, N] is stored at q - in_lo
+        if (!op.in_half) {
+            // input on nodes: node q in [0, N] is stored at q - in_lo
             int q = j;
             sg = 1.0f;
             if (j > N) { q = 2 * N - j; sg = op.s_right; }
             src = q - op.in_lo;
             if (src < 0 || src >= op.nin) src = -1;
         } else {
-            // velocity on half-nodes: m in [0, N) stored at m
+            // input on half-nodes: m in [0, N) stored at m
             src = j;
             sg = 1.0f;
             if (j >= N) { src = 2 * N - 1 - j; sg = op.s_right; }
@@ -260,7 +261,7 @@ PSTD_HD void phase_dense(const LineOp& op, const float* raw, int rs, int G, floa
                          int tid, int nthr) {
     const int nseq = (G + 1) / 2;
     const int total = nseq * op.nout;
-    const int base = op.dir == 0 ? 0 : op.out_lo;
+    const int base = op.out_half ? 0 : op.out_lo;
     for (int t = tid; t < total; t += nthr) {
         const int s = t / op.nout;
         const int i = t - s * op.nout;
@@ -280,7 +281,7 @@ PSTD_HD void phase_dense(const LineOp& op, const float* raw, int rs, int G, floa
 
 // Output value of line g at stored output index i (after the inverse FFT).
 PSTD_HD float op_value(const LineOp& op, const float2* buf, int g, int i) {
-    const int pos = op.dir == 0 ? i : i + op.out_lo;
+    const int pos = op.out_half ? i : i + op.out_lo;
     const float2* seq = buf + (size_t)(g >> 1) * op.seqlen;
     float2 v = seq[pos];
     if (op.kind == 0 && op.group2) v = cmulc(v, PSTD_LDG(&op.shift[pos]));

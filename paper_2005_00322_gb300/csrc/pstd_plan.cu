@@ -98,6 +98,14 @@ struct Axis {
     float2* d_sym = nullptr;          // velocity-spectrum symmetry factors (WAxis::sym)
     float2* d_fUL = nullptr;          // L x the u -> p step coefficients (spectral velocity)
     float* d_ph = nullptr;            // phantom partner lines of unpaired velocity lines
+    // plain differentiation and staggered interpolation (pstd_apply), built on
+    // first use: [op][input field kind]
+    LineOp xop[2][4];
+    int xok[2][4] = {};
+    int xG[2][4] = {};
+    size_t xsmem[2][4] = {};
+    float2* d_xf[2][4] = {};
+    float* d_xdense[2][4] = {};
     WAxis wax{};
     WLaunch wgeo{};
     // split-precision dense form
@@ -380,6 +388,189 @@ std::vector<std::complex<double>> conv_table(const Axis& a, int dir) {
     return h;
 }
 
+// ---- plain differentiation and staggered interpolation (pstd_apply) --------
+// Field kinds along one axis: grid (nodes or half-nodes) and parity class
+// (pressure-like: symmetric at a Neumann wall, antisymmetric at a Dirichlet
+// one; velocity-like: the reverse).  A node where the field is antisymmetric
+// about a wall is zero and not stored.
+struct KindGeo {
+    int half, lo, len;
+    float sR;                 // sign of the field reflected about the right wall
+};
+
+bool kind_geo(const Axis& a, int kind, KindGeo& g) {
+    const bool half = kind == PSTD_HALF_U || kind == PSTD_HALF_P;
+    const bool ppar = kind == PSTD_NODES_P || kind == PSTD_HALF_P;
+    g.half = half ? 1 : 0;
+    if (a.periodic) {
+        g.lo = 0;
+        g.len = a.N;
+        g.sR = 1.0f;
+        return true;
+    }
+    const bool rightS = ppar == (a.bcr == PSTD_NEUMANN);
+    const bool leftS = ppar == (a.bcl == PSTD_NEUMANN);
+    g.sR = rightS ? 1.0f : -1.0f;
+    if (half) {
+        g.lo = 0;
+        g.len = a.N;
+    } else {
+        g.lo = leftS ? 0 : 1;
+        g.len = (rightS ? a.N : a.N - 1) - g.lo + 1;
+    }
+    return g.len > 0;
+}
+
+// Output kind: differentiation keeps the grid and swaps the parity class,
+// interpolation keeps the parity class and swaps the grid (Section 3.3).
+int out_kind(int op, int kind) {
+    static const int diff[4] = {PSTD_NODES_U, PSTD_HALF_P, PSTD_NODES_P, PSTD_HALF_U};
+    static const int interp[4] = {PSTD_HALF_P, PSTD_NODES_U, PSTD_HALF_U, PSTD_NODES_P};
+    return op == PSTD_OP_DIFF ? diff[kind] : interp[kind];
+}
+
+// Folded multiplier of the extension, including 1/L: (i k if `deriv`) times
+// e^{i k shift}; at the Nyquist bin of an even period only its real part,
+// which keeps real lines real (the bin the tables drop or pad with zero).
+std::complex<double> coeff_gen(const Axis& a, int n, bool deriv, double shift) {
+    const int N = a.N, L = a.L;
+    double kap;
+    bool nyquist = false;
+    if (a.periodic) {
+        const int nn = n < (L + 1) / 2 ? n : n - L;
+        kap = 2.0 * M_PI * nn / (L * a.dx);
+        nyquist = (L % 2 == 0 && n == L / 2);
+    } else if (!a.group2) {
+        const int nn = n <= N ? n : n - L;
+        kap = 2.0 * M_PI * nn / (L * a.dx);
+        nyquist = (n == N);
+    } else {
+        const int nn = n < N ? n : n - L;
+        kap = M_PI * (2.0 * nn + 1.0) / (L * a.dx);
+    }
+    std::complex<double> m = std::polar(1.0, kap * shift);
+    if (deriv) m *= std::complex<double>(0.0, kap);
+    if (nyquist) m = m.real();
+    return m / (double)L;
+}
+
+// The convolution-route table of a multiplier f (as conv_table).
+std::vector<std::complex<double>> conv_table_of(const Axis& a, const std::vector<std::complex<double>>& f) {
+    const int L = a.L;
+    std::vector<std::complex<double>> wl(L), h(a.M2, 0.0);
+    for (int n = 0; n < L; ++n)
+        wl[n] = std::complex<double>(std::cos(2.0 * M_PI * n / L), std::sin(2.0 * M_PI * n / L));
+    for (int d = 0; d < L; ++d) {
+        std::complex<double> acc = 0;
+        int64_t idx = 0;
+        for (int n = 0; n < L; ++n) {
+            acc += f[n] * wl[idx];
+            idx += d;
+            if (idx >= L) idx -= L;
+        }
+        if (a.group2) acc *= std::complex<double>(std::cos(M_PI * d / L), std::sin(M_PI * d / L));
+        h[d] = acc;
+    }
+    host_fft(h);
+    for (auto& x : h) x /= (double)a.M2;
+    return h;
+}
+
+// Dense operator (rows: stored outputs, cols: stored inputs) of a multiplier
+// f between two field kinds (as dense_operator64).
+std::vector<float> dense_operator_of(const Axis& a, const std::vector<std::complex<double>>& f, const KindGeo& gi,
+                                     const KindGeo& go) {
+    const int N = a.N, L = a.L;
+    std::vector<std::complex<double>> K(L);
+    for (int d = 0; d < L; ++d) {
+        std::complex<double> acc = 0;
+        for (int n = 0; n < L; ++n) {
+            const double ang = 2.0 * M_PI * (double)((int64_t)d * n % L) / L;
+            acc += f[n] * std::complex<double>(std::cos(ang), std::sin(ang));
+        }
+        K[d] = acc;
+    }
+    std::vector<float> D((size_t)go.len * gi.len);
+    for (int i = 0; i < go.len; ++i) {
+        const int pos = go.half ? i : i + go.lo;
+        for (int j = 0; j < gi.len; ++j) {
+            int src[2];
+            double sg[2];
+            int nimg = 0;
+            if (a.periodic) {
+                src[nimg] = j; sg[nimg++] = 1.0;
+            } else if (!gi.half) {
+                const int q = j + gi.lo;
+                src[nimg] = q; sg[nimg++] = 1.0;
+                if (q > 0 && q < N) { src[nimg] = 2 * N - q; sg[nimg++] = gi.sR; }
+            } else {
+                src[nimg] = j; sg[nimg++] = 1.0;
+                src[nimg] = 2 * N - 1 - j; sg[nimg++] = gi.sR;
+            }
+            double v = 0;
+            for (int m = 0; m < nimg; ++m) {
+                const int delta = pos - src[m];
+                std::complex<double> k = K[((delta % L) + L) % L];
+                if (a.group2) k *= std::complex<double>(std::cos(M_PI * delta / L), std::sin(M_PI * delta / L));
+                v += sg[m] * k.real();
+            }
+            D[(size_t)i * gi.len + j] = (float)v;
+        }
+    }
+    return D;
+}
+
+// Build (once) the line operation `op` on input kind `kind` of axis `i`.
+int build_xop(pstd_plan_s* P, int i, int op, int kind) {
+    Axis& a = P->ax[i];
+    if (a.xok[op][kind]) return PSTD_OK;
+    KindGeo gi, go;
+    const int ok = out_kind(op, kind);
+    if (!kind_geo(a, kind, gi) || !kind_geo(a, ok, go)) return PSTD_EINVAL;
+    const bool deriv = op == PSTD_OP_DIFF;
+    const double shift = gi.half == go.half ? 0.0 : (gi.half ? -0.5 * a.dx : 0.5 * a.dx);
+    std::vector<std::complex<double>> f(a.L);
+    for (int n = 0; n < a.L; ++n) f[n] = coeff_gen(a, n, deriv, shift);
+    LineOp o = a.op[OP_GRAD_P];     // route, FFT plan, shifts, sequence length
+    o.dir = gi.half;
+    o.in_half = gi.half;
+    o.out_half = go.half;
+    o.nin = gi.len;
+    o.nout = go.len;
+    o.in_lo = gi.lo;
+    o.out_lo = go.lo;
+    o.s_right = gi.sR;
+    o.f = nullptr;
+    o.dense = nullptr;
+    int rc;
+    if (a.kind == 0) {
+        std::vector<float2> t(a.L);
+        for (int n = 0; n < a.L; ++n) t[n] = make_float2((float)f[n].real(), (float)f[n].imag());
+        if ((rc = upload(t, &a.d_xf[op][kind])) != PSTD_OK) return rc;
+        o.f = a.d_xf[op][kind];
+    } else if (a.kind == 2) {
+        const std::vector<std::complex<double>> h = conv_table_of(a, f);
+        std::vector<float2> t(a.M2);
+        for (int n = 0; n < a.M2; ++n) t[n] = make_float2((float)h[n].real(), (float)h[n].imag());
+        if ((rc = upload(t, &a.d_xf[op][kind])) != PSTD_OK) return rc;
+        o.f = a.d_xf[op][kind];
+    } else {
+        const std::vector<float> D = dense_operator_of(a, f, gi, go);
+        if ((rc = upload(D, &a.d_xdense[op][kind])) != PSTD_OK) return rc;
+        o.dense = a.d_xdense[op][kind];
+    }
+    int G = 16;
+    while (G > 1 && pstd::cta_smem_bytes(G, o.seqlen, gi.len) > kSmemBudget) --G;
+    const size_t bytes = pstd::cta_smem_bytes(G, o.seqlen, gi.len);
+    if (bytes > 227 * 1024) return PSTD_EUNSUPPORTED;
+    CK(pstd::set_max_smem((int)bytes));
+    a.xop[op][kind] = o;
+    a.xG[op][kind] = G;
+    a.xsmem[op][kind] = bytes;
+    a.xok[op][kind] = 1;
+    return PSTD_OK;
+}
+
 int build_axis(pstd_plan_s* P, int i) {
     Axis& a = P->ax[i];
     const pstd_desc& d = P->desc;
@@ -436,6 +627,8 @@ int build_axis(pstd_plan_s* P, int i) {
         op.L = a.L;
         op.group2 = a.group2;
         op.dir = dir;
+        op.in_half = dir;
+        op.out_half = 1 - dir;
         op.nin = dir == 0 ? a.lp : a.N;
         op.nout = dir == 0 ? a.N : a.lp;
         op.in_lo = a.lo;
@@ -668,6 +861,11 @@ void free_plan_memory(pstd_plan_s* P) {
         cudaFree(a.d_sym);
         cudaFree(a.d_fUL);
         cudaFree(a.d_ph);
+        for (int o = 0; o < 2; ++o)
+            for (int k = 0; k < 4; ++k) {
+                cudaFree(a.d_xf[o][k]);
+                cudaFree(a.d_xdense[o][k]);
+            }
         cudaFree(a.d_gemm);
         for (int o = 0; o < OP_COUNT; ++o) {
             cudaFree(a.d_f[o]);
@@ -989,6 +1187,38 @@ int pstd_field_shape(const pstd_plan_t* P, int field, int64_t shape[3]) {
 int64_t pstd_field_numel(const pstd_plan_t* P, int field) {
     if (!P || field < 0 || field > P->ndim) return 0;
     return P->shape[field][0] * P->shape[field][1] * P->shape[field][2];
+}
+
+int pstd_apply_shape(const pstd_plan_t* P, int axis, int kind, int64_t shape[3]) {
+    if (!P || !shape || axis < 0 || axis >= P->ndim || kind < 0 || kind > 3) return PSTD_EINVAL;
+    KindGeo g;
+    if (!kind_geo(P->ax[axis], kind, g)) return PSTD_EINVAL;
+    for (int j = 0; j < 3; ++j) shape[j] = P->shape[0][j];
+    shape[axis] = g.len;
+    return PSTD_OK;
+}
+
+int pstd_apply(pstd_plan_t* P, int axis, int op, int kind, const float* in, float* out) {
+    if (!P || axis < 0 || axis >= P->ndim || (op != PSTD_OP_DIFF && op != PSTD_OP_INTERP) || kind < 0 ||
+        kind > 3 || !in || !out)
+        return PSTD_EINVAL;
+    P->last_launches = 0;
+    int rc = build_xop(P, axis, op, kind);
+    if (rc != PSTD_OK) return rc;
+    Axis& A = P->ax[axis];
+    GradArgs g;
+    g.op = A.xop[op][kind];
+    g.nlines = A.nlines;
+    g.inner = A.inner;
+    g.G = A.xG[op][kind];
+    g.rs = g.op.nin;
+    g.in = in;
+    g.out = out;
+    g.accumulate = 0;
+    const unsigned grid = (unsigned)((A.nlines + g.G - 1) / g.G);
+    CK(pstd::launch_k_grad(grid, A.xsmem[op][kind], P->stream, g));
+    P->last_launches = 1;
+    return PSTD_OK;
 }
 
 int pstd_grad(pstd_plan_t* P, int axis, int dir, const float* in, float* out) {

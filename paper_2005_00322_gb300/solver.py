@@ -146,6 +146,35 @@ class Solver:
         self._leave()
         return out
 
+    # field kinds and operations of pstd_apply (plain differentiation and
+    # staggered interpolation, Section 3.3)
+    KINDS = {"nodes_p": _abi.NODES_P, "half_u": _abi.HALF_U, "nodes_u": _abi.NODES_U, "half_p": _abi.HALF_P}
+    OUT_KIND = {("diff", "nodes_p"): "nodes_u", ("diff", "nodes_u"): "nodes_p", ("diff", "half_u"): "half_p",
+                ("diff", "half_p"): "half_u", ("interp", "nodes_p"): "half_p", ("interp", "half_p"): "nodes_p",
+                ("interp", "nodes_u"): "half_u", ("interp", "half_u"): "nodes_u"}
+
+    def apply_shape(self, axis: int, kind: str) -> tuple:
+        s = (ctypes.c_int64 * 3)()
+        _abi.check(self.lib, self.lib.pstd_apply_shape(self._h, axis, self.KINDS[kind], s), "pstd_apply_shape")
+        return tuple(int(s[i]) for i in range(self.ndim))
+
+    def apply(self, axis: int, op: str, x, kind: str, out=None):
+        """Plain derivative (op "diff") or interpolation to the other grid (op
+        "interp") along ``axis`` of a field of ``kind``; returns the output."""
+        okind = self.OUT_KIND[(op, kind)]
+        if out is None:
+            out = torch.empty(self.apply_shape(axis, okind), dtype=torch.float32, device=self.device)
+        for t, k, name in ((x, kind, "in"), (out, okind, "out")):
+            if (not isinstance(t, torch.Tensor) or t.device != self.device or t.dtype != torch.float32
+                    or not t.is_contiguous() or tuple(t.shape) != self.apply_shape(axis, k)):
+                raise ValueError(f"{name} must be a contiguous float32 {self.apply_shape(axis, k)} tensor")
+        self._enter()
+        rc = self.lib.pstd_apply(self._h, axis, _abi.OP_DIFF if op == "diff" else _abi.OP_INTERP,
+                                 self.KINDS[kind], ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()))
+        _abi.check(self.lib, rc, "pstd_apply")
+        self._leave()
+        return out
+
     def init_velocity(self, p0, us):
         a, arr = self._t(p0, 0, "p0"), self._us(us)
         self._enter()
