@@ -372,10 +372,13 @@ def learned_main(args) -> None:
             tot += e0.elapsed_time(e1) / 1e3
         return samples * args.steps / tot
 
+    err32 = net.rel_err(net.predict(p0[ntr:], tf32=True), tgt[ntr:]).cpu().numpy()
     xb = p0[:256].contiguous()
     with Clocks(0) as clk:
         net_rate = timed(lambda: net.predict(xb), 256)
         net16_rate = timed(lambda: net.predict(xb, bf16=True), 256)
+        tc_rate = timed(lambda: net.predict(xb, tf32=True), 256)
+    tc_status = net.tensor_core_status()
     # PSTD: one batch plan of 64 members, each bench call loads 64 initial
     # pressures, derives u^{-1/2} and runs the 200 steps
     bt = Batch([dict(ncells=ncells, dx=w.dx, bc=bc, cfl=w.cfl)] * 64)
@@ -400,6 +403,10 @@ def learned_main(args) -> None:
         "speedup_vs_pstd": net_rate / pstd_rate,
         "bf16_weights": {"value": net16_rate, "heldout_max_rel_l2": float(err16.max()),
                          "heldout_mean_rel_l2": float(err16.mean())},
+        "tf32_tensor_cores": {"value": tc_rate, "speedup_vs_pstd": tc_rate / pstd_rate,
+                              "heldout_max_rel_l2": float(err32.max()),
+                              "heldout_mean_rel_l2": float(err32.mean()), "status": tc_status,
+                              "kernel": "k_tc_gemm (tcgen05.mma kind::tf32, TMEM accumulators)"},
         "accuracy": {"heldout": nho, "max_rel_l2": float(err.max()), "mean_rel_l2": float(err.mean()),
                      "judge": "PSTD on the same inputs"},
         "fallback": {"tol": sur.tol, "trusted": sur.trusted, "heldout_max": ho_max},
@@ -421,8 +428,9 @@ def main():
     ap.add_argument("--leapfrog-steps", type=int, default=0, help="override the workload's step count")
     ap.add_argument("--persistent", action="store_true",
                     help="pstd_run as one cooperative kernel with grid barriers")
-    ap.add_argument("--form", default="fft", choices=["fft", "split"],
-                    help="fft: spectral FFT route; split: FP16 hi/lo tensor-core dense form")
+    ap.add_argument("--form", default="fft", choices=["fft", "split", "tensor"],
+                    help="fft: spectral FFT route; split: FP16 hi/lo dense form (mma.sync); "
+                         "tensor: TF32 hi/lo dense form on tcgen05")
     ap.add_argument("--learned", action="store_true",
                     help="train and time the learned operator against 200 PSTD steps (prints its own line)")
     ap.add_argument("--learned-iters", type=int, default=8000)

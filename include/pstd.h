@@ -112,7 +112,12 @@ typedef struct {
      * 1: split-precision dense form -- each derivative as a GEMM with the
      *    FP64-built operator matrix, FP16 hi/lo split products on the tensor
      *    cores with FP32 accumulation (axes with N <= 1024); affects
-     *    pstd_step / pstd_run only. */
+     *    pstd_step / pstd_run only;
+     * 2: tensor-core split form -- the same dense operators as GEMMs on the
+     *    5th-generation tensor cores (tcgen05, kind::tf32): operator and field
+     *    each split into TF32 hi + lo parts, Ah Bh + Ah Bl + Al Bh accumulated
+     *    in FP32 in tensor memory (axes with N <= 1024); a bounded wait that
+     *    gives up is reported by pstd_sync as PSTD_ETIMEOUT. */
     int form;
     /* 1: pstd_run is one cooperative kernel for all its steps, the CTAs
      * meeting at a bounded-wait grid barrier between axis passes (when every
@@ -334,6 +339,14 @@ typedef struct {
     int K_last;
 } pstd_gemm_desc;
 int pstd_nn_gemm(const pstd_gemm_desc* d, void* stream);
+
+/* pstd_nn_gemm on the tensor cores (tcgen05, kind::tf32): A and B are rounded
+ * to TF32 (10-bit mantissa, round to nearest) as they are staged, products
+ * accumulate in FP32 in tensor memory.  Same descriptor and limits as
+ * pstd_nn_gemm except ceil(M / 128) <= 65535.  `status` (device int, may be
+ * NULL) is set to 1 if a bounded wait for the tensor cores gave up; that
+ * tile is then left unwritten.  Errors: PSTD_EINVAL, PSTD_ECUDA. */
+int pstd_nn_gemm_tf32(const pstd_gemm_desc* d, int* status, void* stream);
 
 /* Tensors below are [B][C][P] (B samples, C channels, P points) or [B][P];
  * bias_act, lift and proj_bwd need B C <= 65535, proj B <= 65535.

@@ -47,6 +47,7 @@ SIGNATURES = {
     "pstd_reflection_combos": (c_int, [c_void_p, POINTER(c_double), c_void_p, POINTER(c_double)]),
     "pstd_step_noalloc": (c_int, [c_void_p, c_void_p, POINTER(c_void_p), c_int64, c_void_p]),
     "pstd_nn_gemm": (c_int, [c_void_p, c_void_p]),
+    "pstd_nn_gemm_tf32": (c_int, [c_void_p, c_void_p, c_void_p]),
     "pstd_nn_bias_act": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int, c_int64, c_int, c_void_p]),
     "pstd_nn_act_bwd": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int, c_void_p]),
     "pstd_nn_lift": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int, c_int64, c_void_p]),

@@ -13,6 +13,9 @@ int pstd_internal_launch_steps(pstd_plan_t* P, float* p, float* const* u, int64_
 // spectrum form (to_spectrum != 0) or back; the steps launched by
 // pstd_internal_launch_steps expect the spectrum form.  Adds the kernel count.
 int pstd_internal_convert_velocity(pstd_plan_t* P, float* const* u, int to_spectrum, int64_t* launches);
+// GEMM of the tensor-core split form: pstd_nn_gemm_tf32 with both operands
+// split into TF32 hi + lo parts (B's lo part from B_lo, same strides as B).
+int pstd_internal_tc_gemm_split(const pstd_gemm_desc* d, const float* B_lo, int* status, cudaStream_t st);
 // The plan's stream.
 cudaStream_t pstd_internal_stream(const pstd_plan_t* P);
 // First stored pressure node per axis (0 or 1) and the pressure shape.

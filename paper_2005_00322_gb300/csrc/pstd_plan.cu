@@ -98,6 +98,7 @@ struct Axis {
     float2* d_sym = nullptr;          // velocity-spectrum symmetry factors (WAxis::sym)
     float2* d_fUL = nullptr;          // L x the u -> p step coefficients (spectral velocity)
     float* d_ph = nullptr;            // phantom partner lines of unpaired velocity lines
+    float* d_tc = nullptr;            // tensor-core split form: D1 hi | D1 lo | D2 hi | D2 lo
     // plain differentiation and staggered interpolation (pstd_apply), built on
     // first use: [op][input field kind]
     LineOp xop[2][4];
@@ -809,6 +810,33 @@ int build_axis(pstd_plan_s* P, int i) {
         a.wv = V;
     }
 
+    // tensor-core split form: the dense operators of the two derivatives
+    // (FP64-built, scales folded in) as TF32 hi + lo parts
+    if (P->opts.form == 2) {
+        if (a.N > 1024) return PSTD_EUNSUPPORTED;
+        auto tf32 = [](double x) {
+            float f = (float)x;
+            uint32_t u;
+            std::memcpy(&u, &f, 4);
+            u = (u + 0x1000u) & 0xFFFFE000u;     // round to 10 mantissa bits, ties away
+            std::memcpy(&f, &u, 4);
+            return f;
+        };
+        const std::vector<double> D1 = dense_operator64(a, 0, scales[OP_STEP_P]);   // N x lp
+        const std::vector<double> D2 = dense_operator64(a, 1, scales[OP_STEP_U]);   // lp x N
+        std::vector<float> all;
+        for (const auto* D : {&D1, &D2}) {
+            std::vector<float> hi(D->size()), lo(D->size());
+            for (size_t j = 0; j < D->size(); ++j) {
+                hi[j] = tf32((*D)[j]);
+                lo[j] = tf32((*D)[j] - (double)hi[j]);
+            }
+            all.insert(all.end(), hi.begin(), hi.end());
+            all.insert(all.end(), lo.begin(), lo.end());
+        }
+        if ((rc = upload(all, &a.d_tc)) != PSTD_OK) return rc;
+    }
+
     // split-precision dense form
     if (P->opts.form == 1) {
         if (a.N > 1024) return PSTD_EUNSUPPORTED;
@@ -861,6 +889,7 @@ void free_plan_memory(pstd_plan_s* P) {
         cudaFree(a.d_sym);
         cudaFree(a.d_fUL);
         cudaFree(a.d_ph);
+        cudaFree(a.d_tc);
         for (int o = 0; o < 2; ++o)
             for (int k = 0; k < 4; ++k) {
                 cudaFree(a.d_xf[o][k]);
@@ -930,6 +959,58 @@ StepArgs step_args(pstd_plan_s* P, int a, float* p, float* const* u) {
 int launch_step(pstd_plan_s* P, float* p, float* const* u, int64_t* launches) {
     for (int a = P->ndim - 1; a >= 0; --a) {
         Axis& A = P->ax[a];
+        if (P->opts.form == 2) {
+            // u_a += p D1^T, then acc_out = acc_in + u_a D2^T, as GEMMs over the
+            // lines of the axis (outer blocks as the batch on strided axes)
+            const int64_t inner = A.inner, outer = A.nlines / A.inner;
+            const int N = A.N, lp = A.lp;
+            const size_t n1 = (size_t)N * lp;
+            const float* D1h = A.d_tc;
+            const float* D1l = D1h + n1;
+            const float* D2h = D1l + n1;
+            const float* D2l = D2h + n1;
+            float* acc_in = (a == P->ndim - 1) ? p : P->d_S;
+            float* acc_out = (a == 0) ? p : P->d_S;
+            int* status = (int*)(P->d_sync + 2);
+            auto lines = [&](pstd_gemm_desc& g, const float* X, int xlen, float* Y, int ylen) {
+                if (inner > 1) {
+                    g.batch = outer;
+                    g.M = (int)inner;
+                    g.sAb = (int64_t)xlen * inner; g.sAm = 1; g.sAk = inner;
+                    g.sCb = (int64_t)ylen * inner; g.sCm = 1; g.sCn = inner;
+                } else {
+                    g.batch = 1;
+                    g.M = (int)A.nlines;
+                    g.sAb = 0; g.sAm = xlen; g.sAk = 1;
+                    g.sCb = 0; g.sCm = ylen; g.sCn = 1;
+                }
+                g.A = X;
+                g.C = Y;
+                g.K = xlen;
+                g.N = ylen;
+                g.sBb = 0; g.sBk = 1; g.sBn = xlen;
+                g.alpha = 1.0f;
+                g.beta = 1.0f;
+                g.batch2 = 1;
+                g.K_last = xlen;
+            };
+            pstd_gemm_desc g1{};
+            lines(g1, p, lp, u[a], N);
+            g1.B = D1h;
+            int rc = pstd_internal_tc_gemm_split(&g1, D1l, status, P->stream);
+            if (rc != PSTD_OK) return rc;
+            ++*launches;
+            if (acc_in != acc_out)
+                CK(cudaMemcpyAsync(acc_out, acc_in, (size_t)pstd_field_numel(P, 0) * sizeof(float),
+                                   cudaMemcpyDeviceToDevice, P->stream));
+            pstd_gemm_desc g2{};
+            lines(g2, u[a], N, acc_out, lp);
+            g2.B = D2h;
+            rc = pstd_internal_tc_gemm_split(&g2, D2l, status, P->stream);
+            if (rc != PSTD_OK) return rc;
+            ++*launches;
+            continue;
+        }
         if (P->opts.form == 1) {
             pstd::GemmStep g;
             g.ax = A.gax;
@@ -994,7 +1075,7 @@ int launch_grad(pstd_plan_s* P, int axis, int opi, const float* in, float* out, 
 // dir 2 converts u_a to it in place before the first step, dir 3 back after
 // the last.  Other axes (and the split form) step u_a itself.
 int convert_velocity(pstd_plan_s* P, float* const* u, int dir, int64_t* launches) {
-    if (P->opts.form == 1) return PSTD_OK;
+    if (P->opts.form != 0) return PSTD_OK;
     for (int a = 0; a < P->ndim; ++a) {
         Axis& A = P->ax[a];
         if (!A.wl) continue;
@@ -1093,7 +1174,7 @@ int pstd_plan_ex(const pstd_desc* desc, void* stream, const pstd_plan_opts* opts
     if (!P) return PSTD_ENOMEM;
     P->desc = *desc;
     if (opts) P->opts = *opts;
-    if (P->opts.form != 0 && P->opts.form != 1) {
+    if (P->opts.form < 0 || P->opts.form > 2) {
         delete P;
         return PSTD_EINVAL;
     }
@@ -1113,6 +1194,12 @@ int pstd_plan_ex(const pstd_desc* desc, void* stream, const pstd_plan_opts* opts
         P->shape[f][f - 1] = desc->ncells[f - 1];
     }
     for (int i = 0; i < P->ndim && rc == PSTD_OK; ++i) rc = build_axis(P, i);
+    if (rc == PSTD_OK && P->opts.form == 2) {
+        // status word of the tensor-core GEMMs' bounded waits (read by pstd_sync)
+        cudaError_t e = cudaMalloc((void**)&P->d_sync, 4 * sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMemset(P->d_sync, 0, 4 * sizeof(unsigned));
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(status)");
+    }
     if (rc == PSTD_OK && P->ndim >= 2) {
         cudaError_t e = cudaMalloc((void**)&P->d_S, (size_t)pstd_field_numel(P, 0) * sizeof(float));
         if (e != cudaSuccess) rc = e == cudaErrorMemoryAllocation ? PSTD_ENOMEM : cuda_fail(e, "cudaMalloc(S)");

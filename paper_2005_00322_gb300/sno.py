@@ -80,6 +80,9 @@ class SpectralOperator:
         self.flat, self.gflat, self.m1, self.m2 = z(), z(), z(), z()
         self.params, self.grads = self._views(self.flat), self._views(self.gflat)
         self.adam_steps = 0
+        # tensor-core GEMMs (tcgen05, TF32 operands, FP32 accumulation) when set
+        self.tf32 = False
+        self._status = torch.zeros(1, dtype=torch.int32, device=self.device)
         self._init(seed)
 
     # -- parameters ----------------------------------------------------------
@@ -133,7 +136,16 @@ class SpectralOperator:
         # split: (batch2, sAb2, sBb2, sCb2, K_last) of a chunked reduction
         d = _abi.PstdGemmDesc(batch, M, N, K, A.data_ptr(), *sA, B.data_ptr(), *sB, Cm.data_ptr(), *sC, 1.0, beta,
                               *(split or (1, 0, 0, 0, K)))
-        self._ck(self.lib.pstd_nn_gemm(ctypes.byref(d), self._s()), "pstd_nn_gemm")
+        if self.tf32:
+            self._ck(self.lib.pstd_nn_gemm_tf32(ctypes.byref(d), _ptr(self._status), self._s()), "pstd_nn_gemm_tf32")
+        else:
+            self._ck(self.lib.pstd_nn_gemm(ctypes.byref(d), self._s()), "pstd_nn_gemm")
+
+    def tensor_core_status(self) -> int:
+        """1 if a bounded wait of a tensor-core GEMM gave up since the last call (reset)."""
+        v = int(self._status.item())
+        self._status.zero_()
+        return v
 
     def _empty(self, *shape):
         return torch.empty(shape, dtype=torch.float32, device=self.device)
@@ -151,7 +163,7 @@ class SpectralOperator:
         prm = params or self.params
         B, C, K, X, Y = p0.shape[0], self.C, self.K, self.X, self.Y
         P, KK = X * Y, K * K
-        if B * C > 65535 or (B * C * X + 255) // 256 > 65535:
+        if B * C > 65535 or (B * C * X + 127) // 128 > 65535:
             raise ValueError("batch too large for one pass: split it")
         s = self._s()
         v = self._empty(B, C, X, Y)
@@ -283,8 +295,15 @@ class SpectralOperator:
             self.adam(lr=a)
         return losses.cpu().numpy().tolist()
 
-    def predict(self, p0, chunk=256, bf16=False):
-        """Network output for any batch size (processed in chunks)."""
+    def predict(self, p0, chunk=256, bf16=False, tf32=None):
+        """Network output for any batch size (processed in chunks); tf32 (default:
+        the operator's setting) runs the GEMMs on the tensor cores."""
+        if tf32 is not None and bool(tf32) != self.tf32:
+            saved, self.tf32 = self.tf32, bool(tf32)
+            try:
+                return self.predict(p0, chunk, bf16)
+            finally:
+                self.tf32 = saved
         prm = self.bf16_weights() if bf16 else None
         outs = []
         for i in range(0, p0.shape[0], chunk):

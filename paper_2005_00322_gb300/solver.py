@@ -54,8 +54,8 @@ class Solver:
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
         opts = None
-        if form not in ("fft", "split"):
-            raise ValueError("form is 'fft' or 'split'")
+        if form not in ("fft", "split", "tensor"):
+            raise ValueError("form is 'fft', 'split' or 'tensor'")
         if schedule is not None or form != "fft" or persistent or withhold_arrivals:
             # schedule: per axis (variant, seqs_per_cta), None entries automatic
             opts = _abi.PstdPlanOpts()
@@ -63,7 +63,7 @@ class Solver:
                 v, q = (schedule[i] if schedule and i < len(schedule) and schedule[i] else (None, None))
                 opts.variant[i] = -1 if v is None else int(v)
                 opts.seqs_per_cta[i] = -1 if q is None else int(q)
-            opts.form = 1 if form == "split" else 0
+            opts.form = {"fft": 0, "split": 1, "tensor": 2}[form]
             opts.persistent = 1 if persistent else 0
             opts.spin_limit = int(spin_limit)
             opts.withhold_arrivals = int(withhold_arrivals)

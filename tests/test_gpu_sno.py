@@ -98,6 +98,46 @@ def test_gemm_split_reduction(lib, K, Lc):
         assert lib.pstd_nn_gemm(ctypes.byref(d), None) == -1
 
 
+@pytest.mark.parametrize("M,N,K,batch,la,lb,lc,beta", [
+    (70, 130, 37, 3, "row", "row", "row", 0.0),
+    (128, 64, 32, 1, "col", "row", "row", 0.0),
+    (5, 200, 1, 2, "row", "col", "col", 1.0),
+    (129, 16, 127, 4, "row", "col", "row", 0.0),
+    (32, 33, 300, 5, "inner", "inner", "inner", 1.0),
+    (300, 100, 77, 2, "col", "row", "row", 0.0),
+    (17, 9, 0, 2, "row", "row", "row", 1.0),
+])
+def test_gemm_tf32_tensor_cores(lib, M, N, K, batch, la, lb, lc, beta):
+    """The tcgen05 GEMM (TF32 operands, FP32 accumulation in tensor memory)
+    against FP64 numpy: each product carries at most 2 x 2^-11 relative error
+    from the two roundings to TF32, so the sum of K products is off by at most
+    about 2^-10 sqrt(K) max|a b| for random operands."""
+    rng = np.random.default_rng(M * 1000 + N + K)
+    a, sa, A = _strided(rng, batch, M, K, la)
+    b, sb, B = _strided(rng, batch, K, N, lb)
+    c, sc, C0 = _strided(rng, batch, M, N, lc)
+    ta, tb, tc = _dev(a), _dev(b), _dev(c)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    d = _abi.PstdGemmDesc(batch, M, N, K, ta.data_ptr(), *sa, tb.data_ptr(), *sb, tc.data_ptr(), *sc, 0.75, beta)
+    assert lib.pstd_nn_gemm_tf32(ctypes.byref(d), _p(status), None) == 0
+    torch.cuda.synchronize()
+    assert status.item() == 0
+    ref = 0.75 * np.einsum("bmk,bkn->bmn", A.astype(np.float64), B.astype(np.float64)) + beta * C0
+    got = tc.cpu().numpy()
+    if lc == "row":
+        got = got.reshape(batch, M, N)
+    elif lc == "col":
+        got = got.reshape(batch, N, M).transpose(0, 2, 1)
+    else:
+        got = got.reshape(M, N, batch).transpose(2, 0, 1)
+    amax = np.abs(A).max() if K else 0.0
+    bmax = np.abs(B).max() if K else 0.0
+    tol = 0.75 * 2.0 ** -10 * 4.0 * np.sqrt(max(K, 1)) * amax * bmax + 1e-6 * (np.abs(ref).max() + 1)
+    np.testing.assert_allclose(got, ref, atol=tol)
+    d.batch = 0
+    assert lib.pstd_nn_gemm_tf32(ctypes.byref(d), None, None) == -1
+
+
 def test_gemm_rejects_bad_args(lib):
     t = torch.zeros(4, device="cuda")
     d = _abi.PstdGemmDesc(0, 1, 1, 1, t.data_ptr(), 0, 1, 1, t.data_ptr(), 0, 1, 1, t.data_ptr(), 0, 1, 1, 1.0, 0.0)
@@ -238,6 +278,25 @@ def test_forward_backward_match_oracle(ncells, bc, C, K, L, B):
     for name, ref in g_ref.items():
         got = g[name].cpu().numpy().reshape(ref.shape)
         np.testing.assert_allclose(got, ref, atol=1e-4 * np.abs(ref).max(), err_msg=name)
+
+
+def test_forward_backward_tf32_tensor_cores_match_oracle():
+    """The learned operator with every GEMM on the tensor cores (TF32
+    operands) at its own size: output and gradients within 1% of each
+    tensor's largest entry of the FP64 oracle."""
+    ncells, bc, C, K, L, B = (128, 128), (("N", "N"), ("D", "D")), 32, 16, 4, 2
+    net, prm, bases, p0, tgt = _net_and_oracle(ncells, bc, C, K, L, B, seed=3)
+    net.tf32 = True
+    out_ref, _ = osno.forward(prm, p0.astype(np.float64), *bases, L)
+    _, g_ref = osno.loss_and_grads(prm, p0.astype(np.float64), tgt.astype(np.float64), *bases, L)
+    tp, tt = _dev(p0), _dev(tgt)
+    out = net.forward(tp).cpu().numpy()
+    np.testing.assert_allclose(out, out_ref, atol=1e-2 * np.abs(out_ref).max())
+    _, g = net.loss_and_grads(tp, tt)
+    for name, ref in g_ref.items():
+        got = g[name].cpu().numpy().reshape(ref.shape)
+        np.testing.assert_allclose(got, ref, atol=1e-2 * np.abs(ref).max(), err_msg=name)
+    assert net.tensor_core_status() == 0
 
 
 def test_bf16_weights_close_to_fp32():

@@ -1,4 +1,6 @@
-"""GPU parity of the split-precision dense form (FP16 hi/lo products on tensor cores).
+"""GPU parity of the split-precision dense forms: FP16 hi/lo products on the
+mma.sync tensor-core path ("split") and TF32 hi/lo products on the tcgen05
+tensor cores with accumulators in tensor memory ("tensor").
 
 The same tolerances as the FFT route: 1e-5 relative L2 per step from the same
 state, 1e-4 over a full run, against the FP64 oracle.
@@ -29,12 +31,13 @@ CASES = [((48,), [("N", "N")]), ((100,), [("D", "N")]), ((64, 37), [("D", "D"), 
          ((70, 9), [("N", "N"), ("D", "D")]), ((5, 200), [("D", "D"), ("N", "D")])]
 
 
+@pytest.mark.parametrize("form", ["split", "tensor"])
 @pytest.mark.parametrize("ncells,bcs", CASES)
-def test_split_one_step_matches_oracle(ncells, bcs):
+def test_split_one_step_matches_oracle(ncells, bcs, form):
     from paper_2005_00322_gb300 import Solver
     cfl = 0.25 / np.sqrt(len(ncells))
     dt = pstd.dt_from_cfl(cfl, DX, 1500.0)
-    s = Solver(ncells, DX, bcs, dt=dt, form="split")
+    s = Solver(ncells, DX, bcs, dt=dt, form=form)
     od = pstd.Desc(ncells, (DX,), bcs, dt=dt)
     p0 = inputs.random_field(s.shapes[0], 1).astype(np.float32).astype(np.float64)
     u0 = [inputs.random_field(sh, 2 + i).astype(np.float32).astype(np.float64) * 1e-6
@@ -49,11 +52,12 @@ def test_split_one_step_matches_oracle(ncells, bcs):
     s.close()
 
 
-def test_split_plane512_full_run_vs_modal():
-    """2-D 512^2 DD / NN, 4000 steps of the split form vs the modal closed form."""
+@pytest.mark.parametrize("form", ["split", "tensor"])
+def test_split_plane512_full_run_vs_modal(form):
+    """2-D 512^2 DD / NN, 4000 steps of a split form vs the modal closed form."""
     from paper_2005_00322_gb300 import Solver
     w = inputs.plane512_dx_ny()
-    s = Solver(w.ncells, w.dx, w.bc, cfl=w.cfl, form="split")
+    s = Solver(w.ncells, w.dx, w.bc, cfl=w.cfl, form=form)
     od = pstd.Desc(w.ncells, (w.dx,), w.bc, dt=s.dt)
     p = torch.tensor(np.asarray(s.restrict(w.p0_full()), np.float32), device="cuda")
     us = [torch.zeros(sh, device="cuda") for sh in s.shapes[1:]]
