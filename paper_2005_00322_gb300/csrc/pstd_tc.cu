@@ -139,33 +139,54 @@ __global__ void __launch_bounds__(128) k_tc_gemm(pstd_gemm_desc d, const float* 
     const uint32_t tmem = tmem_slot;
     const uint32_t idesc = idesc_tf32(BM, BN);
 
-    // stage slice s (k0 = s BK) into buffer b
+    // stage slice s (k0 = s BK) into buffer b: every load of this thread is
+    // issued into registers first, then converted and stored, so that the
+    // loads are in flight together
     auto stage = [&](int s, int b) {
         float* Ah = tsm + (size_t)b * TL::STAGE_WORDS;
         float* Al = Ah + TL::A_WORDS;
         float* Bh = SPLIT ? Al + TL::A_WORDS : Al;
         float* Blo = Bh + TL::B_WORDS;
         const int k0 = s * BK;
-        for (int idx = tid; idx < BM * BK; idx += 128) {
+        constexpr int NA = BM * BK / 128, NB = BN * BK / 128;
+        float va[NA], vb[NB], vl[SPLIT ? NB : 1];
+#pragma unroll
+        for (int i = 0; i < NA; ++i) {
+            const int idx = tid + 128 * i;
             const int r = a_kfast ? idx / BK : idx & (BM - 1);
             const int kk = a_kfast ? idx % BK : idx >> 7;
             const int m = m0 + r, k = k0 + kk;
-            const float v = (m < d.M && k < K) ? A[m * d.sAm + k * d.sAk] : 0.0f;
-            const float h = to_tf32(v);
-            const uint32_t o = canon<SPLIT>(r, kk) >> 2;
-            Ah[o] = h;
-            if constexpr (SPLIT) Al[o] = to_tf32(v - h);
+            va[i] = (m < d.M && k < K) ? __ldg(&A[m * d.sAm + k * d.sAk]) : 0.0f;
         }
-        for (int idx = tid; idx < BN * BK; idx += 128) {
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const int idx = tid + 128 * i;
             const int r = b_kfast ? idx / BK : idx & (BN - 1);
             const int kk = b_kfast ? idx % BK : idx >> 6;
             const int n = n0 + r, k = k0 + kk;
             const bool in = n < d.N && k < K;
-            const float v = in ? B[k * d.sBk + n * d.sBn] : 0.0f;
-            const float h = to_tf32(v);
+            vb[i] = in ? __ldg(&B[k * d.sBk + n * d.sBn]) : 0.0f;
+            if constexpr (SPLIT) vl[i] = (in && Bl) ? __ldg(&Bl[k * d.sBk + n * d.sBn]) : 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < NA; ++i) {
+            const int idx = tid + 128 * i;
+            const int r = a_kfast ? idx / BK : idx & (BM - 1);
+            const int kk = a_kfast ? idx % BK : idx >> 7;
+            const float h = to_tf32(va[i]);
+            const uint32_t o = canon<SPLIT>(r, kk) >> 2;
+            Ah[o] = h;
+            if constexpr (SPLIT) Al[o] = to_tf32(va[i] - h);
+        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const int idx = tid + 128 * i;
+            const int r = b_kfast ? idx / BK : idx & (BN - 1);
+            const int kk = b_kfast ? idx % BK : idx >> 6;
+            const float h = to_tf32(vb[i]);
             const uint32_t o = canon<SPLIT>(r, kk) >> 2;
             Bh[o] = h;
-            if constexpr (SPLIT) Blo[o] = to_tf32(Bl ? (in ? Bl[k * d.sBk + n * d.sBn] : 0.0f) : v - h);
+            if constexpr (SPLIT) Blo[o] = to_tf32(Bl ? vl[i] : vb[i] - h);
         }
         // make the staged slices visible to the tensor cores' (async) proxy
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
