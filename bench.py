@@ -89,18 +89,25 @@ def host_threads() -> int:
         return os.cpu_count() or 1
 
 
-def oracle_sample(w, seconds: float, max_steps: int | None = None):
-    """Time the FP64 oracle stepping the full grid of ``w`` for about ``seconds``."""
+def oracle_sample(w, seconds: float, max_steps: int | None = None, order2: bool = False):
+    """Time the FP64 oracle stepping the full grid of ``w`` for about ``seconds``
+    (the coupled leapfrog, or the second-order form with ``order2``)."""
+    from oracle import order2 as o2
     from oracle import pstd
     desc = pstd.Desc(w.ncells, (w.dx,), w.bc, c0=w.c0, rho0=w.rho0,
                      dt=pstd.dt_from_cfl(w.cfl, w.dx, w.c0))
     sl = tuple(slice(j[0], j[-1] + 1) for j in (pstd.p_nodes(n, b) for n, b in zip(w.ncells, w.bc)))
     p0 = w.p0_full()[sl]
-    s = pstd.State(p0, pstd.init_velocity(desc, p0, None))
-    s = pstd.step(desc, s)                       # warm the BLAS pools
+    if order2:
+        s = (p0, o2.init_prev(desc, p0))
+        step = lambda st: o2.step(desc, *st)
+    else:
+        s = pstd.State(p0, pstd.init_velocity(desc, p0, None))
+        step = lambda st: pstd.step(desc, st)
+    s = step(s)                                  # warm the BLAS pools
     n, t0 = 0, time.perf_counter()
     while True:
-        s = pstd.step(desc, s)
+        s = step(s)
         n += 1
         el = time.perf_counter() - t0
         if (max_steps and n >= max_steps) or (not max_steps and el >= seconds):
@@ -208,39 +215,59 @@ class SingleRunner:
         import torch
         from paper_2005_00322_gb300 import Solver
         self.w = w
-        self.solver = Solver(w.ncells, w.dx, w.bc, c0=w.c0, rho0=w.rho0, cfl=w.cfl, form=form,
-                             persistent=persistent)
+        # order2: the second-order pressure-only form (pstd_init_prev / pstd_run2)
+        self.order2 = form == "order2"
+        self.solver = Solver(w.ncells, w.dx, w.bc, c0=w.c0, rho0=w.rho0, cfl=w.cfl,
+                             form="fft" if self.order2 else form, persistent=persistent)
         self.stream = self.solver.stream
         p0 = np.asarray(self.solver.restrict(w.p0_full()), np.float32)
         self.p0 = torch.tensor(p0, device="cuda")
         self.p, self.us = self.solver.zeros()
-        self.host_in = [torch.from_numpy(p0).pin_memory()] + \
-            [torch.zeros(sh, dtype=torch.float32).pin_memory() for sh in self.solver.shapes[1:]]
-        self.host_out = [torch.empty_like(h).pin_memory() for h in self.host_in]
+        if self.order2:
+            self.us = [torch.zeros_like(self.p)]          # p^{n-1}
+            self.host_in = [torch.from_numpy(p0).pin_memory()]
+            self.host_out = [torch.empty_like(self.host_in[0]).pin_memory() for _ in range(2)]
+        else:
+            self.host_in = [torch.from_numpy(p0).pin_memory()] + \
+                [torch.zeros(sh, dtype=torch.float32).pin_memory() for sh in self.solver.shapes[1:]]
+            self.host_out = [torch.empty_like(h).pin_memory() for h in self.host_in]
         self.cells = cells(w)
         self.ndim = w.ndim
         self.launches_per_step = w.ndim
+        # fields read and written once per step at the algorithmic minimum
+        self.fields = 2 if self.order2 else w.ndim + 1
+
+    def _start(self):
+        if self.order2:
+            self.solver.init_prev(self.p, self.us[0])
+        else:
+            self.solver.init_velocity(self.p, self.us)
+
+    def _run(self, n):
+        if self.order2:
+            self.solver.run2(self.p, self.us[0], n)
+        else:
+            self.solver.run(self.p, self.us, n)
 
     def step(self):
         self.p.copy_(self.p0)
         for u in self.us:
             u.zero_()
-        self.solver.init_velocity(self.p, self.us)
+        self._start()
         n = self.solver.last_launch_count()
-        self.solver.run(self.p, self.us, self.w.steps)
+        self._run(self.w.steps)
         return n + self.solver.last_launch_count()
 
     def step_e2e(self):
-        dev = [self.p] + self.us
-        for d, h in zip(dev, self.host_in):
+        for d, h in zip([self.p] + self.us, self.host_in):
             d.copy_(h, non_blocking=True)
-        self.solver.init_velocity(self.p, self.us)
-        self.solver.run(self.p, self.us, self.w.steps)
-        for h, d in zip(self.host_out, dev):
+        self._start()
+        self._run(self.w.steps)
+        for h, d in zip(self.host_out, [self.p] + self.us):
             h.copy_(d, non_blocking=True)
 
     def leapfrog(self, n):
-        self.solver.run(self.p, self.us, n)
+        self._run(n)
 
     def close(self):
         self.solver.close()
@@ -428,9 +455,10 @@ def main():
     ap.add_argument("--leapfrog-steps", type=int, default=0, help="override the workload's step count")
     ap.add_argument("--persistent", action="store_true",
                     help="pstd_run as one cooperative kernel with grid barriers")
-    ap.add_argument("--form", default="fft", choices=["fft", "split", "tensor"],
+    ap.add_argument("--form", default="fft", choices=["fft", "split", "tensor", "order2"],
                     help="fft: spectral FFT route; split: FP16 hi/lo dense form (mma.sync); "
-                         "tensor: TF32 hi/lo dense form on tcgen05")
+                         "tensor: TF32 hi/lo dense form on tcgen05; order2: second-order "
+                         "pressure-only form on the FFT passes")
     ap.add_argument("--learned", action="store_true",
                     help="train and time the learned operator against 200 PSTD steps (prints its own line)")
     ap.add_argument("--learned-iters", type=int, default=8000)
@@ -508,7 +536,8 @@ def main():
         return a0.elapsed_time(a1) / 1e3
     run_time(32)
     step_s = (run_time(96) - run_time(32)) / 64
-    alg_step = sum(2 * (len(m) + 1) * 4 * int(np.prod(m)) for m in
+    nfields = (lambda m: run.fields) if single else (lambda m: len(m) + 1)
+    alg_step = sum(2 * nfields(m) * 4 * int(np.prod(m)) for m in
                    ([mm.ncells for mm in members_of(w)] if single or isinstance(w, list)
                     else [w.ncells] * len(run.weights)))
     if single:
@@ -522,12 +551,17 @@ def main():
     traffic = None
     if os.path.exists(TRAFFIC):
         tr = json.load(open(TRAFFIC))
-        ent = tr.get(args.workload)
+        # counters belong to the kernel that ran: the fused step pass, or the
+        # kernel of another form (key "<workload>/<form>")
+        variant = args.form if args.form != "fft" else ("persistent" if args.persistent else "")
+        ent = tr.get(args.workload + ("/" + variant if variant else ""))
         if ent and ent.get("csrc_digest") == csrc_digest():
             traffic = ent.get("dram_bytes_per_launch")
     achieved = alg_bytes / per_launch / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "k_wstep (fused axis pass)",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "k_wgrad dir 4 (second-order axis pass)" if args.form == "order2"
+                else "k_wstep (fused axis pass)",
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
                 "alg_bytes_per_launch": alg_bytes,
                 "launch_s": per_launch if single else None, "step_s": step_s}
@@ -548,9 +582,11 @@ def main():
     cpu = None
     if rank == 0 and world == 1:
         wc = w0 if single or isinstance(w, list) else inputs.cube256(bc=(("N", "N"),) * 3)
-        n, el = oracle_sample(wc, args.cpu_seconds)
+        o2 = args.form == "order2" and single
+        n, el = oracle_sample(wc, args.cpu_seconds, order2=o2)
         cpu = {"value": cells(wc) * n / el, "unit": UNIT, "cores": host_threads(), "kind": "oracle",
-               "sample": f"{n} FP64 leapfrog steps of the full {wc.name} grid ({el:.1f} s)"}
+               "sample": f"{n} FP64 {'second-order' if o2 else 'leapfrog'} steps of the full {wc.name} grid "
+                         f"({el:.1f} s)"}
 
     if rank == 0:
         nmem = 1 if single else (len(w) if isinstance(w, list) else len(run.weights))

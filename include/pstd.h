@@ -194,8 +194,8 @@ const char* pstd_last_cuda_error(void);
 double pstd_dt_from_cfl(double cfl, double dx, double c0);
 
 /* Number of kernels the last pstd_step / pstd_run / pstd_grad /
- * pstd_init_velocity call on this plan launched (graph replays count their
- * kernel nodes). */
+ * pstd_init_velocity / pstd_apply / pstd_init_prev / pstd_run2 call on this
+ * plan launched (graph replays count their kernel nodes). */
 int64_t pstd_last_launch_count(const pstd_plan_t* plan);
 
 /* Library version string. */
@@ -233,6 +233,39 @@ int pstd_apply_shape(const pstd_plan_t* plan, int axis, int kind, int64_t shape[
  * FP64 on first use of (axis, op, kind) and kept by the plan.
  * Errors: PSTD_EINVAL, PSTD_ENOMEM, PSTD_ECUDA, PSTD_EUNSUPPORTED. */
 int pstd_apply(pstd_plan_t* plan, int axis, int op, int kind, const float* in, float* out);
+
+/* ---- Second-order pressure-only form ---------------------------------------- */
+/* Writing the pressure update of Eq. (dtt_pstd_solution) (n-D form of
+ * Section 4.3) at two consecutive steps and subtracting removes the velocity:
+ *   p^{n+1} = 2 p^n - p^{n-1} + (c0 dt)^2 sum_i D_{u,i} D_{p,i} p^n,
+ * with D_{p,i} = T_{i,2}^{-1} a_{i,1} T_{i,1} and D_{u,i} = T_{i,1}^{-1} a_{i,2}
+ * T_{i,2} of Table 2.  It needs two pressure-shaped fields instead of ndim + 1
+ * and equals the coupled leapfrog's pressure when p^{-1} is the pressure that
+ * run had one step before p^0 (pstd_init_prev).  The composed operator is the
+ * real multiplier -k^2 on each axis's symmetric-periodic extension, evaluated
+ * on the same routes as the staggered derivatives; its tables are built in
+ * FP64 on first use and kept by the plan.  Plans of any form accept these
+ * calls (the split forms' dense operators are not used). */
+
+/* p^{-1} of a run from p^0 with zero initial velocity, into `p_prev`
+ * (pressure-shaped device buffers that must not overlap):
+ *   desc->uinit == PSTD_U_AS_GIVEN (u^{-1/2} = 0):  p^{-1} = p^0
+ *   desc->uinit == PSTD_U_HALFSTEP (Section 4.2's half-step start):
+ *     p^{-1} = p^0 + (c0 dt)^2 / 2 sum_i D_{u,i} D_{p,i} p^0.
+ * Errors: PSTD_EINVAL, PSTD_ENOMEM, PSTD_ECUDA. */
+int pstd_init_prev(pstd_plan_t* plan, const float* p0, float* p_prev);
+
+/* `nsteps` >= 0 steps of the second-order form in place: on entry p holds p^n
+ * and p_prev p^{n-1}; on return p holds p^{n+nsteps} and p_prev
+ * p^{n+nsteps-1} (pressure-shaped device buffers that must not overlap).
+ * During the run the p_prev buffer carries q = p^n - p^{n-1} (converted on
+ * entry and back on return): the recurrence becomes q += (c0 dt)^2 sum_i
+ * D_{u,i} D_{p,i} p, p += q, which keeps FP32 rounding in the low modes from
+ * being amplified by 1 / (omega dt) as the 2 p^n - p^{n-1} form would.  One
+ * pass per axis and step, last axis first (the pass of axis 0 also updates
+ * p); blocks of steps are graph-replayed per (p, p_prev) pair as in pstd_run.
+ * Errors: PSTD_EINVAL, PSTD_ENOMEM, PSTD_ECUDA. */
+int pstd_run2(pstd_plan_t* plan, float* p, float* p_prev, int64_t nsteps);
 
 /* ---- Batched runs and reflection coefficients (Section 5) ------------------ */
 

@@ -9,7 +9,9 @@
 //    updated u_a line from shared memory for the second derivative.  acc is
 //    the running pressure sum over axes (p^n for the first axis processed,
 //    the scratch accumulator in between, p^{n+1} for the last).
-//  * cta_grad: out <- (accumulate ? out : 0) + f(in), one derivative.
+//  * cta_grad: out <- (accumulate ? out : 0) + f(in), one derivative (or,
+//        for the second-order form, the composed operator on the pressure
+//        nodes, optionally followed by pout <- in + out).
 //
 // Line l of an axis with stride `inner` (the product of the later extents)
 // starts at (l / inner) * len * inner + (l % inner) in a field with `len`
@@ -50,6 +52,8 @@ struct GradArgs {
     const float* in;
     float* out;
     int accumulate;
+    float* pout = nullptr;  // input and output on one grid: also write in + (the new out)
+                            // here (may be `in`: each entry belongs to one line)
 };
 
 PSTD_HD int64_t line_base(int64_t l, int64_t inner, int len) {
@@ -181,7 +185,9 @@ PSTD_HD void cta_grad(const GradArgs& a, int64_t block, void* smem, int tid, int
         item(t, Gv, len, a.inner, g, i);
         const int64_t idx = line_base(l0 + g, a.inner, len) + (int64_t)i * a.inner;
         const float v = op_value(a.op, y, g, i);
-        a.out[idx] = a.accumulate ? a.out[idx] + v : v;
+        const float r = a.accumulate ? a.out[idx] + v : v;
+        a.out[idx] = r;
+        if (a.pout) a.pout[idx] = a.in[idx] + r;
     }
 }
 

@@ -18,6 +18,21 @@ __global__ void __launch_bounds__(kThreads) k_grad(GradArgs a) {
     cta_grad(a, blockIdx.x, smem_f4, threadIdx.x, blockDim.x);
 }
 
+// y <- alpha x + beta y (the second-order form's change of variables).
+__global__ void __launch_bounds__(kThreads) k_axpby(int64_t n, float alpha, const float* x, float beta, float* y) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        y[i] = fmaf(alpha, x[i], beta * y[i]);
+}
+
+cudaError_t launch_k_axpby(int64_t n, float alpha, const float* x, float beta, float* y, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n + kThreads - 1) / kThreads;
+    if (blocks > 8 * 152) blocks = 8 * 152;
+    k_axpby<<<(unsigned)blocks, kThreads, 0, st>>>(n, alpha, x, beta, y);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_k_step(unsigned grid, size_t smem, cudaStream_t st, const StepArgs& a) {
     k_step<<<grid, kThreads, smem, st>>>(a);
     return cudaGetLastError();

@@ -34,6 +34,7 @@ namespace pstd {
 cudaError_t launch_k_step(unsigned grid, size_t smem, cudaStream_t st, const StepArgs& a);
 cudaError_t launch_k_grad(unsigned grid, size_t smem, cudaStream_t st, const GradArgs& a);
 cudaError_t set_max_smem(int bytes);
+cudaError_t launch_k_axpby(int64_t n, float alpha, const float* x, float beta, float* y, cudaStream_t st);
 // register-FFT passes, one dispatcher per translation unit (pstd_wkernels_*.cu)
 cudaError_t wsmall_step(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WStep& a);
 cudaError_t wsmall_grad(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WGrad& a);
@@ -107,6 +108,12 @@ struct Axis {
     size_t xsmem[2][4] = {};
     float2* d_xf[2][4] = {};
     float* d_xdense[2][4] = {};
+    // second-order form (pstd_run2), built on first use: (c0 dt)^2 D_u D_p
+    // on the pressure nodes
+    int ok2 = 0;
+    LineOp op2{};
+    float2* d_f2 = nullptr;
+    float* d_dense2 = nullptr;
     WAxis wax{};
     WLaunch wgeo{};
     // split-precision dense form
@@ -149,6 +156,7 @@ bool wtw(int L, int V, std::vector<float2>& out) {
 }
 
 struct GraphEntry {
+    int kind = 0;                     // 0: leapfrog steps (u: velocities), 1: second-order steps (u[0]: q)
     float* p = nullptr;
     float* u[3] = {nullptr, nullptr, nullptr};
     cudaGraphExec_t exec = nullptr;
@@ -572,6 +580,50 @@ int build_xop(pstd_plan_s* P, int i, int op, int kind) {
     return PSTD_OK;
 }
 
+// ---- second-order pressure-only form (pstd_run2) ----------------------------
+// Eliminating u from the leapfrog gives p^{n+1} = 2 p^n - p^{n-1}
+// + (c0 dt)^2 sum_a D_{u,a} D_{p,a} p^n.  On the extension D_u D_p is the
+// product of the two staggered multipliers, -kappa^2 (the half-cell shifts
+// cancel, and at the Nyquist bin the real parts multiply to the same value),
+// so each axis needs one real table on the pressure nodes.
+int build_order2(pstd_plan_s* P, int i) {
+    Axis& a = P->ax[i];
+    if (a.ok2) return PSTD_OK;
+    const pstd_desc& d = P->desc;
+    const double s2 = (d.c0 * d.dt) * (d.c0 * d.dt);
+    std::vector<std::complex<double>> f(a.L);
+    for (int n = 0; n < a.L; ++n)
+        f[n] = (coeff(a, n, 0, 1.0) * coeff(a, n, 1, 1.0) * (double)a.L * s2).real();
+    KindGeo g;
+    if (!kind_geo(a, PSTD_NODES_P, g)) return PSTD_EINVAL;
+    LineOp o = a.op[OP_GRAD_P];     // route, FFT plan, shifts, sequence length
+    o.dir = 0;
+    o.in_half = 0;
+    o.out_half = 0;
+    o.nin = g.len;
+    o.nout = g.len;
+    o.in_lo = g.lo;
+    o.out_lo = g.lo;
+    o.s_right = g.sR;
+    o.f = nullptr;
+    o.dense = nullptr;
+    int rc;
+    if (a.kind == 0 || a.kind == 2) {
+        const std::vector<std::complex<double>> h = a.kind == 0 ? f : conv_table_of(a, f);
+        std::vector<float2> t(h.size());
+        for (size_t n = 0; n < h.size(); ++n) t[n] = make_float2((float)h[n].real(), (float)h[n].imag());
+        if ((rc = upload(t, &a.d_f2)) != PSTD_OK) return rc;
+        o.f = a.d_f2;
+    } else {
+        const std::vector<float> D = dense_operator_of(a, f, g, g);
+        if ((rc = upload(D, &a.d_dense2)) != PSTD_OK) return rc;
+        o.dense = a.d_dense2;
+    }
+    a.op2 = o;
+    a.ok2 = 1;
+    return PSTD_OK;
+}
+
 int build_axis(pstd_plan_s* P, int i) {
     Axis& a = P->ax[i];
     const pstd_desc& d = P->desc;
@@ -890,6 +942,8 @@ void free_plan_memory(pstd_plan_s* P) {
         cudaFree(a.d_fUL);
         cudaFree(a.d_ph);
         cudaFree(a.d_tc);
+        cudaFree(a.d_f2);
+        cudaFree(a.d_dense2);
         for (int o = 0; o < 2; ++o)
             for (int k = 0; k < 4; ++k) {
                 cudaFree(a.d_xf[o][k]);
@@ -1068,6 +1122,98 @@ int launch_grad(pstd_plan_s* P, int axis, int opi, const float* in, float* out, 
     g.accumulate = acc;
     const unsigned grid = (unsigned)((A.nlines + A.G - 1) / A.G);
     CK(pstd::launch_k_grad(grid, A.smem, P->stream, g));
+    return PSTD_OK;
+}
+
+// One second-order pass of `axis`: out += (c0 dt)^2 D_u D_p in along the
+// axis, and pout = in + out (the new value) where pout is given.
+int launch_order2(pstd_plan_s* P, int axis, const float* in, float* out, float* pout) {
+    Axis& A = P->ax[axis];
+    if (A.wl) {
+        WGrad g{};
+        g.ax = A.wax;
+        g.dir = 4;
+        g.f = A.d_f2;
+        g.in = in;
+        g.out = out;
+        g.accumulate = 1;
+        g.scale = 1.0f;
+        g.pout = pout;
+        CK(wgrad(A.L, A.wv, A.strided, A.wgeo, P->stream, g));
+        return PSTD_OK;
+    }
+    GradArgs g;
+    g.op = A.op2;
+    g.nlines = A.nlines;
+    g.inner = A.inner;
+    g.G = A.G;
+    g.rs = A.rs;
+    g.in = in;
+    g.out = out;
+    g.accumulate = 1;
+    g.pout = pout;
+    const unsigned grid = (unsigned)((A.nlines + A.G - 1) / A.G);
+    CK(pstd::launch_k_grad(grid, A.smem, P->stream, g));
+    return PSTD_OK;
+}
+
+// One second-order step on (p, q = p^n - p^{n-1}), last axis first:
+// q += (c0 dt)^2 sum_a D_{u,a} D_{p,a} p, and the pass of axis 0 also writes
+// p = p + q.  Each pass reads p^n, which only the last pass overwrites, and
+// that pass writes each p line after the CTA that owns it has read it.
+int launch_order2_step(pstd_plan_s* P, float* p, float* q, int64_t* launches) {
+    for (int a = P->ndim - 1; a >= 0; --a) {
+        int rc = launch_order2(P, a, p, q, a == 0 ? p : nullptr);
+        if (rc != PSTD_OK) return rc;
+        ++*launches;
+    }
+    return PSTD_OK;
+}
+
+// Replay graphs of kGraphSteps steps for this pointer set (kind 0: leapfrog
+// steps on p and the velocities; kind 1: second-order steps on p and q),
+// recording one on first use (least recently used entry replaced); `done`
+// counts the steps replayed.
+template <class StepFn>
+int replay_graphs(pstd_plan_t* P, int kind, float* p, float* const* u, int nu, int64_t nsteps, int64_t& done,
+                  StepFn&& one_step) {
+    GraphEntry* ge = nullptr;
+    for (auto& g : P->graphs) {
+        bool same = g.exec && g.kind == kind && g.p == p;
+        for (int a = 0; a < nu && same; ++a) same = g.u[a] == u[a];
+        if (same) { ge = &g; break; }
+    }
+    if (!ge) {
+        GraphEntry* victim = &P->graphs[0];
+        for (auto& g : P->graphs) {
+            if (!g.exec) { victim = &g; break; }
+            if (g.stamp < victim->stamp) victim = &g;
+        }
+        if (victim->exec) { cudaGraphExecDestroy(victim->exec); victim->exec = nullptr; }
+        CK(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal));
+        int64_t nl = 0;
+        int rc = PSTD_OK;
+        for (int s = 0; s < kGraphSteps && rc == PSTD_OK; ++s) rc = one_step(&nl);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(P->stream, &graph);
+        if (rc != PSTD_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&victim->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) { victim->exec = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+        victim->kind = kind;
+        victim->p = p;
+        for (int a = 0; a < 3; ++a) victim->u[a] = a < nu ? u[a] : nullptr;
+        victim->steps = kGraphSteps;
+        victim->launches = nl;
+        ge = victim;
+    }
+    ge->stamp = ++P->stamp;
+    while (nsteps - done >= ge->steps) {
+        CK(cudaGraphLaunch(ge->exec, P->stream));
+        done += ge->steps;
+        P->last_launches += ge->launches;
+    }
     return PSTD_OK;
 }
 
@@ -1391,43 +1537,9 @@ int run_steps(pstd_plan_t* P, float* p, float* const* u, int64_t nsteps) {
     }
     int64_t done = 0;
     if (P->stream != nullptr && nsteps >= kGraphSteps) {
-        // find or record the graph of kGraphSteps steps for this pointer set
-        GraphEntry* ge = nullptr;
-        for (auto& g : P->graphs) {
-            bool same = g.exec && g.p == p;
-            for (int a = 0; a < P->ndim && same; ++a) same = g.u[a] == u[a];
-            if (same) { ge = &g; break; }
-        }
-        if (!ge) {
-            GraphEntry* victim = &P->graphs[0];
-            for (auto& g : P->graphs) {
-                if (!g.exec) { victim = &g; break; }
-                if (g.stamp < victim->stamp) victim = &g;
-            }
-            if (victim->exec) { cudaGraphExecDestroy(victim->exec); victim->exec = nullptr; }
-            CK(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal));
-            int64_t nl = 0;
-            int rc = PSTD_OK;
-            for (int s = 0; s < kGraphSteps && rc == PSTD_OK; ++s) rc = launch_step(P, p, u, &nl);
-            cudaGraph_t graph = nullptr;
-            cudaError_t e = cudaStreamEndCapture(P->stream, &graph);
-            if (rc != PSTD_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
-            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-            e = cudaGraphInstantiate(&victim->exec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (e != cudaSuccess) { victim->exec = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
-            victim->p = p;
-            for (int a = 0; a < 3; ++a) victim->u[a] = a < P->ndim ? u[a] : nullptr;
-            victim->steps = kGraphSteps;
-            victim->launches = nl;
-            ge = victim;
-        }
-        ge->stamp = ++P->stamp;
-        while (nsteps - done >= ge->steps) {
-            CK(cudaGraphLaunch(ge->exec, P->stream));
-            done += ge->steps;
-            P->last_launches += ge->launches;
-        }
+        int rc = replay_graphs(P, 0, p, u, P->ndim, nsteps, done,
+                               [&](int64_t* nl) { return launch_step(P, p, u, nl); });
+        if (rc != PSTD_OK) return rc;
     }
     while (done < nsteps) {
         int rc = launch_step(P, p, u, &P->last_launches);
@@ -1437,6 +1549,61 @@ int run_steps(pstd_plan_t* P, float* p, float* const* u, int64_t nsteps) {
     return PSTD_OK;
 }
 }  // namespace
+
+int pstd_init_prev(pstd_plan_t* P, const float* p0, float* p_prev) {
+    if (!P || !p0 || !p_prev || p0 == p_prev) return PSTD_EINVAL;
+    P->last_launches = 0;
+    const int64_t n = pstd_field_numel(P, 0);
+    if (P->desc.uinit == PSTD_U_AS_GIVEN) {
+        // u^{-1/2} = 0: p^{-1} = p^0
+        CK(cudaMemcpyAsync(p_prev, p0, (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, P->stream));
+        return PSTD_OK;
+    }
+    // half-step start: p^{-1} = p^0 + (c0 dt)^2 / 2 sum_a D_{u,a} D_{p,a} p^0
+    for (int a = 0; a < P->ndim; ++a) {
+        int rc = build_order2(P, a);
+        if (rc != PSTD_OK) return rc;
+    }
+    CK(cudaMemsetAsync(p_prev, 0, (size_t)n * sizeof(float), P->stream));
+    for (int a = P->ndim - 1; a >= 0; --a) {
+        int rc = launch_order2(P, a, p0, p_prev, nullptr);
+        if (rc != PSTD_OK) return rc;
+        ++P->last_launches;
+    }
+    CK(pstd::launch_k_axpby(n, 1.0f, p0, 0.5f, p_prev, P->stream));
+    ++P->last_launches;
+    return PSTD_OK;
+}
+
+int pstd_run2(pstd_plan_t* P, float* p, float* p_prev, int64_t nsteps) {
+    if (!P || !p || !p_prev || p == p_prev || nsteps < 0) return PSTD_EINVAL;
+    P->last_launches = 0;
+    if (nsteps == 0) return PSTD_OK;
+    for (int a = 0; a < P->ndim; ++a) {
+        int rc = build_order2(P, a);
+        if (rc != PSTD_OK) return rc;
+    }
+    // carry q = p^n - p^{n-1} in the p_prev buffer during the run
+    const int64_t n = pstd_field_numel(P, 0);
+    float* q = p_prev;
+    CK(pstd::launch_k_axpby(n, 1.0f, p, -1.0f, q, P->stream));
+    int64_t conv = 1;
+    int64_t done = 0;
+    if (P->stream != nullptr && nsteps >= kGraphSteps) {
+        int rc = replay_graphs(P, 1, p, &q, 1, nsteps, done,
+                               [&](int64_t* nl) { return launch_order2_step(P, p, q, nl); });
+        if (rc != PSTD_OK) return rc;
+    }
+    while (done < nsteps) {
+        int rc = launch_order2_step(P, p, q, &P->last_launches);
+        if (rc != PSTD_OK) return rc;
+        ++done;
+    }
+    CK(pstd::launch_k_axpby(n, 1.0f, p, -1.0f, q, P->stream));   // p^{n-1} = p^n - q
+    ++conv;
+    P->last_launches += conv;
+    return PSTD_OK;
+}
 
 int pstd_sync(pstd_plan_t* P) {
     if (!P) return PSTD_EINVAL;

@@ -116,12 +116,14 @@ struct WStep {
 
 struct WGrad {
     WAxis ax;
-    int dir;                 // 0: p -> u, 1: u -> p, 2: u -> its spectrum, 3: spectrum -> u
+    int dir;                 // 0: p -> u, 1: u -> p, 2: u -> its spectrum, 3: spectrum -> u,
+                             // 4: p -> p (the second-order form's composed operator)
     const float2* f;
     const float* in;
     float* out;
     int accumulate;
     float scale;             // dir 2: 1 / L
+    float* pout = nullptr;   // dir 4: also write in + (the new out) here (may be `in`)
 };
 
 // A line with no partner (odd line count) still has a complex spectrum:
@@ -516,7 +518,8 @@ PSTD_HD void grad_contig(const WGrad& a, int64_t block, float2* smem, int tid, i
     const float2* f = a.f;
     const float2* none = nullptr;
     float2* bufs = stage_tables<S>(A, f, none, smem, tid, nthr);
-    const auto tab = tables<S>(A, a.dir == 0 ? f : nullptr, a.dir == 0 ? nullptr : f, t);
+    const bool from_p = a.dir == 0 || a.dir == 4;   // input on the pressure nodes
+    const auto tab = tables<S>(A, from_p ? f : nullptr, from_p ? nullptr : f, t);
     async_wait_all();
     PSTD_SYNCCTA();
     pdl_wait();
@@ -524,7 +527,7 @@ PSTD_HD void grad_contig(const WGrad& a, int64_t block, float2* smem, int tid, i
     const int64_t la = 2 * seq, lb = 2 * seq + 1;
     const bool va = la < A.nlines, vb = lb < A.nlines;
     float2* sm = bufs + (size_t)sq * wf::seq_words<S::L>();
-    if (a.dir >= 2) {
+    if (a.dir == 2 || a.dir == 3) {
         // spectrum side of an unpaired line: the phantom partner
         const bool ph = !vb && va && A.ph;
         const bool rb = vb || (ph && a.dir == 3), wb = vb || (ph && a.dir == 2);
@@ -540,25 +543,38 @@ PSTD_HD void grad_contig(const WGrad& a, int64_t block, float2* smem, int tid, i
                         });
         return;
     }
-    const int nin = a.dir == 0 ? A.lp : A.N;
+    const int nin = from_p ? A.lp : A.N;
     const int nout = a.dir == 0 ? A.N : A.lp;
     const float* xa = a.in + (va ? la : 0) * nin;
     const float* xb = a.in + (vb ? lb : 0) * nin;
     float2 v[E];
     auto src = [&](int i) { return make_float2(va ? xa[i] : 0.0f, vb ? xb[i] : 0.0f); };
-    if (a.dir == 0) derivative<S, 0>(v, t, sm, A, tab, src);
+    if (from_p) derivative<S, 0>(v, t, sm, A, tab, src);
     else derivative<S, 1>(v, t, sm, A, tab, src);
     float* oa = a.out + (va ? la : 0) * nout;
     float* ob = a.out + (vb ? lb : 0) * nout;
     const int off = a.dir == 0 ? 0 : A.lo;
+    // dir 4 with pout: the sequence's reads of `in` all precede the FFT's
+    // barriers, so pout may be `in` (each node belongs to one line)
+    float* qa = a.pout ? a.pout + (va ? la : 0) * nin : nullptr;
+    float* qb = a.pout ? a.pout + (vb ? lb : 0) * nin : nullptr;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int i = t + T * e - off;
         if (i >= 0 && i < nout) {
-            if (va) oa[i] = a.accumulate ? oa[i] + v[e].x : v[e].x;
-            if (vb) ob[i] = a.accumulate ? ob[i] + v[e].y : v[e].y;
+            if (va) {
+                const float y = a.accumulate ? oa[i] + v[e].x : v[e].x;
+                oa[i] = y;
+                if (qa) qa[i] = xa[i] + y;
+            }
+            if (vb) {
+                const float y = a.accumulate ? ob[i] + v[e].y : v[e].y;
+                ob[i] = y;
+                if (qb) qb[i] = xb[i] + y;
+            }
         }
     }
+    pdl_trigger();
 }
 
 // ---- strided layout ---------------------------------------------------------
@@ -692,12 +708,13 @@ PSTD_HD void grad_strided(const WGrad& a, int64_t block, float2* smem0, int tid,
     float2* smem = stage_tables<S>(A, f, none, smem0, tid, nthr);
     int sq, t;
     lane_of<S>(tid, sq, t);
-    const auto tab = tables<S>(A, a.dir == 0 ? f : nullptr, a.dir == 0 ? nullptr : f, t);
+    const bool from_p = a.dir == 0 || a.dir == 4;   // input on the pressure nodes
+    const auto tab = tables<S>(A, from_p ? f : nullptr, from_p ? nullptr : f, t);
     int64_t o, i0;
     int Gv;
     tile_of(A, block, o, i0, Gv);
-    const int nin = a.dir == 0 ? A.lp : A.N;
-    const int nout = a.dir == 0 || a.dir >= 2 ? A.N : A.lp;
+    const int nin = from_p ? A.lp : A.N;
+    const int nout = a.dir == 0 || a.dir == 2 || a.dir == 3 ? A.N : A.lp;
     float* rawI = (float*)(smem + (size_t)A.seqs * wf::seq_words<S::L>());
     float* rawO = rawI + (size_t)A.G * row_stride(nin);
     pdl_wait();
@@ -705,7 +722,7 @@ PSTD_HD void grad_strided(const WGrad& a, int64_t block, float2* smem0, int tid,
     if (a.accumulate) tile_load(a.out, nout, A, o, i0, Gv, rawO, tid, nthr);
     async_wait_all();
     PSTD_SYNCCTA();
-    if (a.dir >= 2) {
+    if (a.dir == 2 || a.dir == 3) {
         // in place through the tile: rawO is a separate buffer of the same
         // shape.  An odd tile's last line pairs with the phantom row Gv: read
         // from WAxis::ph (dir 3) or written to it (dir 2).
@@ -745,22 +762,36 @@ PSTD_HD void grad_strided(const WGrad& a, int64_t block, float2* smem0, int tid,
         const float* xb = rawI + (vb ? gb : 0) * row_stride(nin);
         float2 v[E];
         auto src = [&](int i) { return make_float2(va ? xa[i] : 0.0f, vb ? xb[i] : 0.0f); };
-        if (a.dir == 0) derivative<S, 0>(v, t, sm, A, tab, src);
+        if (from_p) derivative<S, 0>(v, t, sm, A, tab, src);
         else derivative<S, 1>(v, t, sm, A, tab, src);
         float* oa = rawO + (va ? ga : 0) * row_stride(nout);
         float* ob = rawO + (vb ? gb : 0) * row_stride(nout);
+        // dir 4 with pout: the input rows become in + out in place (this
+        // sequence's reads of them precede the FFT's barriers)
+        float* ia = rawI + (va ? ga : 0) * row_stride(nin);
+        float* ib = rawI + (vb ? gb : 0) * row_stride(nin);
         const int off = a.dir == 0 ? 0 : A.lo;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int i = t + T * e - off;
             if (i >= 0 && i < nout) {
-                if (va) oa[i] = a.accumulate ? oa[i] + v[e].x : v[e].x;
-                if (vb) ob[i] = a.accumulate ? ob[i] + v[e].y : v[e].y;
+                if (va) {
+                    const float y = a.accumulate ? oa[i] + v[e].x : v[e].x;
+                    oa[i] = y;
+                    if (a.pout) ia[i] += y;
+                }
+                if (vb) {
+                    const float y = a.accumulate ? ob[i] + v[e].y : v[e].y;
+                    ob[i] = y;
+                    if (a.pout) ib[i] += y;
+                }
             }
         }
     }
     PSTD_SYNCCTA();
     tile_store(a.out, nout, A, o, i0, Gv, rawO, tid, nthr);
+    if (a.pout) tile_store(a.pout, nin, A, o, i0, Gv, rawI, tid, nthr);
+    pdl_trigger();
 }
 
 }  // namespace wk

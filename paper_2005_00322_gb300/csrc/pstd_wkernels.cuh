@@ -77,6 +77,9 @@ cudaError_t wlaunch_step(bool strided, const WLaunch& g, cudaStream_t st, const 
 }
 template <int L, int V>
 cudaError_t wlaunch_grad(bool strided, const WLaunch& g, cudaStream_t st, const WGrad& a) {
+    // the second-order form's passes follow one another: overlap each launch
+    // with the previous pass's drain, as the leapfrog passes do
+    if (a.dir == 4) return launch_pdl(strided ? k_wgrad_s<L, V> : k_wgrad_c<L, V>, g, st, a);
     if (strided) k_wgrad_s<L, V><<<g.grid, g.threads, g.smem, st>>>(a);
     else k_wgrad_c<L, V><<<g.grid, g.threads, g.smem, st>>>(a);
     return cudaGetLastError();

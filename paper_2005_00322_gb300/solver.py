@@ -193,6 +193,22 @@ class Solver:
         _abi.check(self.lib, self.lib.pstd_run(self._h, a, arr, int(nsteps)), "pstd_run")
         self._leave()
 
+    def init_prev(self, p0, p_prev):
+        """p^{-1} into ``p_prev`` for the second-order form, from p^0 with zero
+        initial velocity (the plan's uinit reading)."""
+        a, b = self._t(p0, 0, "p0"), self._t(p_prev, 0, "p_prev")
+        self._enter()
+        _abi.check(self.lib, self.lib.pstd_init_prev(self._h, a, b), "pstd_init_prev")
+        self._leave()
+
+    def run2(self, p, p_prev, nsteps: int):
+        """``nsteps`` steps of the second-order pressure-only form in place:
+        (p^n, p^{n-1}) -> (p^{n+nsteps}, p^{n+nsteps-1})."""
+        a, b = self._t(p, 0, "p"), self._t(p_prev, 0, "p_prev")
+        self._enter()
+        _abi.check(self.lib, self.lib.pstd_run2(self._h, a, b, int(nsteps)), "pstd_run2")
+        self._leave()
+
     def sync(self):
         _abi.check(self.lib, self.lib.pstd_sync(self._h), "pstd_sync")
 
