@@ -18,6 +18,16 @@ inverse DTT.  This module covers the eight SPS types of groups I and II
     HSHA       half   m = 0..N-1                                          C4
     HAHS       half   m = 0..N-1                                          S4
 
+and the eight of groups III and IV (types V-VIII, odd period M = 2N - 1):
+an axis with a node wall at x = 0 and a mid-cell wall at x = (N - 1/2) dx,
+pressure-like nodes j = 0..N-1 and half-nodes m = 0..N-1 (m = N-1 lies on
+the mid-cell wall):
+
+    WSHS  nodes j = 0..N-1  C5      HSWS  half m = 0..N-1  C6
+    WAHA  nodes j = 1..N-1  S5      HAWA  half m = 0..N-2  S6
+    WSHA  nodes j = 0..N-1  C7      HSWA  half m = 0..N-2  C8
+    WAHS  nodes j = 1..N-1  S7      HAWS  half m = 0..N-1  S8
+
 Differentiation keeps the grid and swaps S <-> A at both walls; the k-space
 operation is -k (cosine -> sine) or +k (sine -> cosine).  Interpolation
 keeps the symmetry and swaps the grid (W <-> H); the k-space operation is the
@@ -52,11 +62,32 @@ SYMMETRY = {
     "HAHA": (True, "S2", True, False),
     "HSHA": (True, "C4", False, True),
     "HAHS": (True, "S4", True, True),
+    "WSHS": (False, "C5", False, False),
+    "WAHA": (False, "S5", True, False),
+    "WSHA": (False, "C7", False, True),
+    "WAHS": (False, "S7", True, True),
+    "HSWS": (True, "C6", False, False),
+    "HAWA": (True, "S6", True, False),
+    "HSWA": (True, "C8", False, True),
+    "HAWS": (True, "S8", True, True),
 }
 
 
+def mid_wall(sym: str) -> bool:
+    """Groups III and IV: one wall at a node, the other at mid-cell."""
+    return sym[0] != sym[2]
+
+
+def period(sym: str, n: int) -> int:
+    """M = 2N (groups I, II) or 2N - 1 (groups III, IV)."""
+    return 2 * n - 1 if mid_wall(sym) else 2 * n
+
+
 def sample_length(sym: str, n: int) -> int:
-    """Representative samples of a symmetry on an axis of n cells."""
+    """Representative samples of a symmetry on an axis of n cells (groups
+    III / IV: n nodes, the mid-cell wall at (n - 1/2) dx)."""
+    if mid_wall(sym):
+        return n - 1 if sym in ("WAHA", "WAHS", "HAWA", "HSWA") else n
     return {"WSWS": n + 1, "WAWA": n - 1}.get(sym, n)
 
 
@@ -64,7 +95,7 @@ def positions(sym: str, n: int, dx: float) -> np.ndarray:
     """Coordinates of the representative samples."""
     half = SYMMETRY[sym][0]
     if half:
-        return (np.arange(n) + 0.5) * dx
+        return (np.arange(sample_length(sym, n)) + 0.5) * dx
     first = 0 if sym[1] == "S" else 1
     return (np.arange(sample_length(sym, n)) + first) * dx
 
@@ -94,7 +125,7 @@ def _apply(sym_in: str, sym_out: str, f: np.ndarray, n: int, dx: float, deriv: b
     f = np.asarray(f, np.float64)
     if f.shape[-1] != sample_length(sym_in, n):
         raise ValueError(f"{sym_in} on {n} cells has {sample_length(sym_in, n)} samples")
-    M = 2 * n
+    M = period(sym_in, n)
     _, T_in, sine_in, _ = SYMMETRY[sym_in]
     _, T_out, _, _ = SYMMETRY[sym_out]
     U = dtt.apply(T_in, f, -1)
@@ -124,3 +155,11 @@ def interp(sym: str, f: np.ndarray, n: int, dx: float):
     """(values on the other grid, their symmetry): Tables A2 and A5."""
     out = interp_symmetry(sym)
     return _apply(sym, out, f, n, dx, False), out
+
+
+def stagger(sym: str, f: np.ndarray, n: int, dx: float):
+    """(derivative on the other grid, its symmetry): differentiation and
+    interpolation in one k-space operation (Tables A3 and A6), the staggered
+    derivative of the PSTD step."""
+    out = interp_symmetry(diff_symmetry(sym))
+    return _apply(sym, out, f, n, dx, True), out

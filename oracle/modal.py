@@ -26,8 +26,8 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import dtt
-from .pstd import TABLE2, Desc, p_nodes
+from . import dtt, dtt_ops
+from .pstd import Desc, mid_wall, p_nodes, symmetries, t1_of, u_len
 
 
 def mode_wavenumbers(n: int, bc: tuple, dx: float) -> np.ndarray:
@@ -37,8 +37,11 @@ def mode_wavenumbers(n: int, bc: tuple, dx: float) -> np.ndarray:
     if bc == ("P", "P"):
         from .pstd import fourier_wavenumbers
         return fourier_wavenumbers(n, dx)
+    if mid_wall(bc):    # groups III / IV: M = 2N - 1
+        sym = symmetries(bc)[0]
+        return 2.0 * np.pi * dtt_ops.wavenumber_index(sym, n) / (dtt_ops.period(sym, n) * dx)
     L = n * dx
-    T1 = TABLE2[bc][0]
+    T1 = t1_of(bc)
     if T1 == "C1":      # n = 0..N
         return np.pi * np.arange(0, n + 1) / L
     if T1 == "S1":      # n = 1..N-1
@@ -65,8 +68,8 @@ def _forward(bc, P, axis):
         n = P.shape[axis]
         return np.moveaxis(np.moveaxis(P, axis, -1) @ dft_matrix(n).T, -1, axis)
     if np.iscomplexobj(P):      # a periodic axis was transformed already
-        return dtt.apply(TABLE2[bc][0], P.real, axis) + 1j * dtt.apply(TABLE2[bc][0], P.imag, axis)
-    return dtt.apply(TABLE2[bc][0], P, axis)
+        return dtt.apply(t1_of(bc), P.real, axis) + 1j * dtt.apply(t1_of(bc), P.imag, axis)
+    return dtt.apply(t1_of(bc), P, axis)
 
 
 def _inverse(bc, P, axis):
@@ -75,8 +78,8 @@ def _inverse(bc, P, axis):
         n = P.shape[axis]
         return np.moveaxis((np.moveaxis(P, axis, -1) @ np.conj(dft_matrix(n)).T) / n, -1, axis)
     if np.iscomplexobj(P):
-        return dtt.inverse(TABLE2[bc][0], P.real, axis) + 1j * dtt.inverse(TABLE2[bc][0], P.imag, axis)
-    return dtt.inverse(TABLE2[bc][0], P, axis)
+        return dtt.inverse(t1_of(bc), P.real, axis) + 1j * dtt.inverse(t1_of(bc), P.imag, axis)
+    return dtt.inverse(t1_of(bc), P, axis)
 
 
 def modal_pressure(desc: Desc, p0: np.ndarray, nsteps: int, uinit: str = "halfstep") -> np.ndarray:
@@ -111,7 +114,7 @@ def separable_modal_pressure(desc: Desc, factors: list, nsteps: int,
     for term in factors:
         t = None
         for i in range(desc.ndim):
-            f = dtt.apply(TABLE2[desc.bc[i]][0], np.asarray(term[i], np.float64))
+            f = dtt.apply(t1_of(desc.bc[i]), np.asarray(term[i], np.float64))
             t = f if t is None else np.multiply.outer(t, f)
         spec = t if spec is None else spec + t
     if uinit == "halfstep":
@@ -119,7 +122,7 @@ def separable_modal_pressure(desc: Desc, factors: list, nsteps: int,
     else:
         spec = spec * np.cos((nsteps + 0.5) * wdt) / np.cos(0.5 * wdt)
     for i in range(desc.ndim):
-        T1 = TABLE2[desc.bc[i]][0]
+        T1 = t1_of(desc.bc[i])
         n = spec.shape[i]
         Minv = dtt.dtt_matrix(dtt.inverse_partner(T1), n) / dtt.implied_period(T1, n)
         if out_index is not None and out_index[i] is not None:
@@ -141,12 +144,21 @@ def node_weights(n: int, bc: tuple) -> np.ndarray:
     return w
 
 
+def half_weights(n: int, bc: tuple) -> np.ndarray:
+    """Weight of each stored velocity half-node: 1/2 on the one a Dirichlet
+    mid-cell wall passes through (u symmetric there), 1 elsewhere."""
+    w = np.ones(u_len(n, bc))
+    if mid_wall(bc) and bc[1] == "Dm":
+        w[-1] = 0.5
+    return w
+
+
 def _weights(desc: Desc, field: int) -> np.ndarray:
     """Tensor-product weights of p (field 0) or u_i (field i+1)."""
     w = None
     for a in range(desc.ndim):
         if field == a + 1:
-            wa = np.ones(desc.ncells[a])
+            wa = half_weights(desc.ncells[a], desc.bc[a])
         else:
             wa = node_weights(desc.ncells[a], desc.bc[a])
         w = wa if w is None else np.multiply.outer(w, wa)

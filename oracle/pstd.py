@@ -29,6 +29,14 @@ Readings where the paper is silent (each listed in the design notes):
   nodes x_j = j dx with walls at j = 0 and j = N, velocity on the N half-nodes
   (m + 1/2) dx.  Only the pressure nodes that are not on a Dirichlet wall are
   stored (Dirichlet wall pressure is identically zero).
+* Groups III and IV of Table 1 (types V-VIII, odd period M = 2N - 1) describe
+  an axis whose right wall lies half a cell past the last node, at
+  x = (N - 1/2) dx, with nodes j = 0..N-1 (bc "Nm" or "Dm" on the right).
+  The pressure symmetry is W?H? (WSHS, WSHA, WAHS, WAHA: C5, C7, S7, S5) and
+  the velocity's H?W? (HAWA, HAWS, HSWA, HSWS: S6, S8, C8, C6); the staggered
+  derivatives apply the same rule as Tables A3/A6 (``dtt_ops.stagger``).  The
+  velocity half-node on the mid-cell wall is stored only where u is symmetric
+  about it (Dirichlet), so u has N - 1 (Neumann) or N (Dirichlet) samples.
 * The initial half-step velocity either equals the given u0
   (``uinit="as_given"``) or is u^{-1/2} = u0 + (dt / (2 rho0)) D_p p^0
   (``uinit="halfstep"``), which makes the time-centred velocity equal u0 at
@@ -42,11 +50,13 @@ from typing import Sequence
 
 import numpy as np
 
-from . import dtt
+from . import dtt, dtt_ops
 
 NEUMANN = "N"
 DIRICHLET = "D"
 PERIODIC = "P"      # Table 2's periodic row: the Fourier PSTD method of Section 2
+NEUMANN_MID = "Nm"  # right wall at mid-cell, x = (N - 1/2) dx (Table 1 groups III / IV)
+DIRICHLET_MID = "Dm"
 
 # Table 2: (left, right) -> (T1, T2, sign of a1, sign of a2)
 TABLE2 = {
@@ -79,15 +89,47 @@ class Desc:
             raise ValueError("ncells, dx and bc must have one entry per axis")
 
 
+def mid_wall(bc: tuple) -> bool:
+    """The right wall lies half a cell past node N - 1 (types V-VIII)."""
+    return bc[1] in (NEUMANN_MID, DIRICHLET_MID)
+
+
+def symmetries(bc: tuple):
+    """(pressure SPS, velocity SPS) of a walled axis (Table 2; groups III / IV
+    for a mid-cell right wall)."""
+    left = "S" if bc[0] == NEUMANN else "A"
+    if mid_wall(bc):
+        sym_p = "W" + left + "H" + ("S" if bc[1] == NEUMANN_MID else "A")
+    else:
+        sym_p = "W" + left + "W" + ("S" if bc[1] == NEUMANN else "A")
+    return sym_p, dtt_ops.interp_symmetry(dtt_ops.diff_symmetry(sym_p))
+
+
+def t1_of(bc: tuple) -> str:
+    """The pressure transform T1 of a walled axis."""
+    if mid_wall(bc):
+        return dtt_ops.SYMMETRY[symmetries(bc)[0]][1]
+    return TABLE2[bc][0]
+
+
 def p_nodes(n: int, bc: tuple) -> np.ndarray:
     """Indices j of the stored pressure nodes x_j = j dx (Dirichlet walls dropped).
 
-    A periodic axis stores the N nodes j = 0..N-1 (node N is node 0)."""
+    A periodic axis stores the N nodes j = 0..N-1 (node N is node 0); an axis
+    with a mid-cell right wall the nodes up to N - 1."""
     if bc == (PERIODIC, PERIODIC):
         return np.arange(0, n)
     lo = 1 if bc[0] == DIRICHLET else 0
-    hi = n - 1 if bc[1] == DIRICHLET else n
+    hi = n - 1 if (bc[1] == DIRICHLET or mid_wall(bc)) else n
     return np.arange(lo, hi + 1)
+
+
+def u_len(n: int, bc: tuple) -> int:
+    """Stored velocity half-nodes along the axis (N, or N - 1 next to a
+    Neumann mid-cell wall, where u vanishes on the wall)."""
+    if mid_wall(bc):
+        return dtt_ops.sample_length(symmetries(bc)[1], n)
+    return n
 
 
 def p_len(n: int, bc: tuple) -> int:
@@ -100,7 +142,7 @@ def field_shapes(desc: Desc):
     shapes = [tuple(plen)]
     for i in range(desc.ndim):
         s = list(plen)
-        s[i] = desc.ncells[i]
+        s[i] = u_len(desc.ncells[i], desc.bc[i])
         shapes.append(tuple(s))
     return shapes
 
@@ -146,6 +188,9 @@ def grad_p(p: np.ndarray, axis: int, n: int, bc: tuple, dx: float) -> np.ndarray
     """T2^{-1}{ a1 T1{p} } along ``axis``: pressure nodes -> velocity half-nodes."""
     if bc == (PERIODIC, PERIODIC):
         return fourier_grad(p, axis, n, dx, +0.5 * dx)
+    if mid_wall(bc):
+        pm = np.moveaxis(np.asarray(p, np.float64), axis, -1)
+        return np.moveaxis(dtt_ops.stagger(symmetries(bc)[0], pm, n, dx)[0], -1, axis)
     T1, T2, s1, _ = TABLE2[bc]
     M = 2 * n
     k = wavenumbers(n, bc, dx)
@@ -170,6 +215,9 @@ def grad_u(u: np.ndarray, axis: int, n: int, bc: tuple, dx: float) -> np.ndarray
     """T1^{-1}{ a2 T2{u} } along ``axis``: velocity half-nodes -> pressure nodes."""
     if bc == (PERIODIC, PERIODIC):
         return fourier_grad(u, axis, n, dx, -0.5 * dx)
+    if mid_wall(bc):
+        um = np.moveaxis(np.asarray(u, np.float64), axis, -1)
+        return np.moveaxis(dtt_ops.stagger(symmetries(bc)[1], um, n, dx)[0], -1, axis)
     T1, T2, _, s2 = TABLE2[bc]
     M = 2 * n
     k = wavenumbers(n, bc, dx)

@@ -1,7 +1,7 @@
 """Pins of the DTT differentiation and interpolation oracle (Tables A1, A2,
-A4, A5): single modes map exactly to their derivative / their values on the
-other grid, and interpolation after differentiation is the staggered
-derivative of Table 2."""
+A4, A5), for the sixteen symmetries of Table 1 (groups I-IV): single modes
+map exactly to their derivative / their values on the other grid, and
+interpolation after differentiation is the staggered derivative of Table 2."""
 import numpy as np
 import pytest
 
@@ -11,7 +11,7 @@ DX = 1e-4
 
 
 def _mode(sym, nv, n, x):
-    k = 2.0 * np.pi * nv / (2 * n * DX)
+    k = 2.0 * np.pi * nv / (dtt_ops.period(sym, n) * DX)
     sine = dtt_ops.SYMMETRY[sym][2]
     return (np.sin(k * x) if sine else np.cos(k * x)), k, sine
 
