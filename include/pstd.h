@@ -49,8 +49,24 @@ extern "C" {
  * walls of an axis) is Table 2's periodic row, the Fourier PSTD method of
  * Section 2 (Eq. fourier_pstd_solution): the axis stores the N nodes
  * j = 0..N-1 and its derivatives are i k e^{+-i k dx/2} with the DFT
- * wavenumbers of Section 2. */
-typedef enum { PSTD_NEUMANN = 0, PSTD_DIRICHLET = 1, PSTD_PERIODIC = 2 } pstd_bc;
+ * wavenumbers of Section 2.
+ * PSTD_NEUMANN_MID / PSTD_DIRICHLET_MID (right wall only, N >= 2): the wall
+ * lies half a cell past the last node, at x = (N - 1/2) dx, so the axis
+ * stores the nodes up to N - 1 and its symmetric-periodic extension has odd
+ * period M = 2N - 1: groups III and IV of Table 1 (types V-VIII; pressure
+ * WSHS / WSHA / WAHS / WAHA, velocity HAWA / HAWS / HSWA / HSWS).  The
+ * velocity half-node on the wall is stored only next to a Dirichlet wall
+ * (u is symmetric there), so u_axis has N - 1 (Neumann) or N entries along
+ * its axis.  These axes run on the generic FFT route (3- and 5-smooth M),
+ * the convolution route or the dense route; plans with a split form
+ * (pstd_plan_opts.form 1, 2) reject them with PSTD_EUNSUPPORTED. */
+typedef enum {
+    PSTD_NEUMANN = 0,
+    PSTD_DIRICHLET = 1,
+    PSTD_PERIODIC = 2,
+    PSTD_NEUMANN_MID = 3,
+    PSTD_DIRICHLET_MID = 4
+} pstd_bc;
 
 /* How pstd_init_velocity derives u^{-1/2} from the given u(0).
  * PSTD_U_HALFSTEP: u^{-1/2} = u0 + (dt / (2 rho0)) D_p p^0, so that the

@@ -8,7 +8,9 @@ from ctypes import POINTER, c_char_p, c_double, c_float, c_int, c_int64, c_void_
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libpstd.so")
 
-NEUMANN, DIRICHLET, PERIODIC = 0, 1, 2
+NEUMANN, DIRICHLET, PERIODIC, NEUMANN_MID, DIRICHLET_MID = 0, 1, 2, 3, 4
+# wall codes: "Nm" / "Dm" put the right wall at mid-cell, x = (N - 1/2) dx
+BC_CODES = {"N": NEUMANN, "D": DIRICHLET, "P": PERIODIC, "Nm": NEUMANN_MID, "Dm": DIRICHLET_MID}
 U_HALFSTEP, U_AS_GIVEN = 0, 1
 NODES_P, HALF_U, NODES_U, HALF_P = 0, 1, 2, 3
 OP_DIFF, OP_INTERP = 0, 1
@@ -137,7 +139,8 @@ def check(lib, code: int, what: str) -> None:
 
 
 def make_desc(ncells, dx, bc, c0, rho0, dt, uinit=U_HALFSTEP) -> PstdDesc:
-    """Build a pstd_desc; bc per axis is a pair of "N"/"D" (or 0/1)."""
+    """Build a pstd_desc; bc per axis is a pair of "N" / "D" / "P" (right wall
+    also "Nm" / "Dm": at mid-cell), or their codes."""
     d = PstdDesc()
     d.ndim = len(ncells)
     dxs = list(dx) if hasattr(dx, "__len__") else [dx]
@@ -149,7 +152,7 @@ def make_desc(ncells, dx, bc, c0, rho0, dt, uinit=U_HALFSTEP) -> PstdDesc:
         for s in range(2):
             if i < d.ndim:
                 b = bc[i][s]
-                d.bc[i][s] = {"N": NEUMANN, "D": DIRICHLET, "P": PERIODIC}.get(b, b) if isinstance(b, str) else int(b)
+                d.bc[i][s] = BC_CODES.get(b, b) if isinstance(b, str) else int(b)
             else:
                 d.bc[i][s] = NEUMANN
     d.c0, d.rho0, d.dt, d.uinit = float(c0), float(rho0), float(dt), int(uinit)

@@ -192,6 +192,7 @@ extern "C" int pstd_step_noalloc(const pstd_desc* d, float* p, float* const* u, 
             op = pstd::LineOp{};
             op.kind = 0;
             op.N = N;
+            op.R2 = 2 * N;
             op.L = L;
             op.group2 = bcl != bcr;
             op.dir = dir;

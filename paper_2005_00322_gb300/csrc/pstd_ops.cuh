@@ -62,6 +62,9 @@ struct LineOp {
     int dir;                // 0: pressure nodes -> half-nodes, 1: half-nodes -> nodes
     int in_half, out_half;  // grid of the input / output: 0 nodes, 1 half-nodes
     int nin, nout;          // stored input / output line lengths
+    int R2;                 // twice the right wall's position in cells: 2N (wall at a node),
+                            // 2N - 1 (wall at mid-cell, Table 1 groups III / IV); the
+                            // reflection about it maps node j to R2 - j, half-node m to R2 - 1 - m
     int in_lo;              // input on nodes: first stored node (0 or 1)
     int out_lo;             // output on nodes: first stored node (0 or 1)
     float s_right;          // sign of the input reflected about the right wall
@@ -221,17 +224,19 @@ PSTD_HD void phase_extend(const LineOp& op, const float* raw, int rs, int G, flo
         int src;
         float sg;
         if (!op.in_half) {
-            // input on nodes: node q in [0, N] is stored at q - in_lo
+            // input on nodes: node q (2 q <= R2) is stored at q - in_lo
             int q = j;
             sg = 1.0f;
-            if (j > N) { q = 2 * N - j; sg = op.s_right; }
+            if (2 * j > op.R2) { q = op.R2 - j; sg = op.s_right; }
             src = q - op.in_lo;
             if (src < 0 || src >= op.nin) src = -1;
         } else {
-            // input on half-nodes: m in [0, N) stored at m
+            // input on half-nodes: m (2 m + 1 <= R2) stored at m; a half-node on
+            // a mid-cell wall past the stored ones is a zero
             src = j;
             sg = 1.0f;
-            if (j >= N) { src = 2 * N - 1 - j; sg = op.s_right; }
+            if (2 * j + 1 > op.R2) { src = op.R2 - 1 - j; sg = op.s_right; }
+            if (src >= op.nin) src = -1;
         }
         const int g0 = 2 * s, g1 = 2 * s + 1;
         float re = 0.0f, im = 0.0f;

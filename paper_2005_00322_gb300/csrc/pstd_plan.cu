@@ -81,6 +81,10 @@ enum { OP_GRAD_P = 0, OP_GRAD_U = 1, OP_STEP_P = 2, OP_STEP_U = 3, OP_INIT_P = 4
 struct Axis {
     int N = 0, L = 0, group2 = 0, kind = 0, M2 = 0, periodic = 0;
     int lp = 0, lo = 0;               // stored pressure length, first stored node
+    int mid = 0;                      // right wall at mid-cell, x = (N - 1/2) dx (types V-VIII)
+    int R2 = 0;                       // twice the right wall's position in cells (2N or 2N - 1)
+    int nu = 0;                       // stored velocity half-nodes (N, or N - 1 next to a
+                                      // Neumann mid-cell wall)
     double dx = 0;
     int bcl = 0, bcr = 0;
     FftPlan fft{};
@@ -223,23 +227,33 @@ namespace {
 
 // Folded coefficient f_n of the extension's Fourier multiplier (Table 1
 // wavenumbers; shift +dx/2 for p -> u, -dx/2 for u -> p), including 1/M.
-std::complex<double> coeff(const Axis& a, int n, int dir, double scale) {
-    const int N = a.N, L = a.L;
-    double kap;
-    bool nyquist = false;
+// Wavenumber of bin n of the extension's FFT and whether it is the Nyquist
+// bin (the bin that pairs with itself, whose value is real for real lines).
+// Period L = M: 2N (groups I, II), 2N - 1 (groups III, IV: odd), N (periodic).
+// Periodic groups: k = 2 pi n / (L dx); antiperiodic groups, pre-twiddled:
+// k = pi (2n + 1) / (L dx); n above the middle stands for n - L.
+double wavenumber(const Axis& a, int n, bool& nyquist) {
+    const int L = a.L;
     if (a.periodic) {
-        // period L = N: n in [-N/2, N/2 - 1] (even N), [-(N-1)/2, (N-1)/2] (odd)
+        // n in [-N/2, N/2 - 1] (even N), [-(N-1)/2, (N-1)/2] (odd)
         const int nn = n < (L + 1) / 2 ? n : n - L;
-        kap = 2.0 * M_PI * nn / (L * a.dx);
         nyquist = (L % 2 == 0 && n == L / 2);
-    } else if (!a.group2) {
-        const int nn = n <= N ? n : n - L;
-        kap = 2.0 * M_PI * nn / (L * a.dx);
-        nyquist = (n == N);
-    } else {
-        const int nn = n < N ? n : n - L;
-        kap = M_PI * (2.0 * nn + 1.0) / (L * a.dx);
+        return 2.0 * M_PI * nn / (L * a.dx);
     }
+    if (!a.group2) {
+        const int nn = 2 * n <= L ? n : n - L;
+        nyquist = 2 * n == L;
+        return 2.0 * M_PI * nn / (L * a.dx);
+    }
+    const int nn = 2 * n + 1 <= L ? n : n - L;
+    nyquist = 2 * n + 1 == L;
+    return M_PI * (2.0 * nn + 1.0) / (L * a.dx);
+}
+
+std::complex<double> coeff(const Axis& a, int n, int dir, double scale) {
+    const int L = a.L;
+    bool nyquist = false;
+    const double kap = wavenumber(a, n, nyquist);
     const double s = dir == 0 ? 0.5 * a.dx : -0.5 * a.dx;
     // i kap exp(i kap s) = (-kap sin(kap s), kap cos(kap s))
     double re = -kap * std::sin(kap * s);
@@ -267,14 +281,17 @@ std::vector<double> dense_operator64(const Axis& a, int dir, double scale) {
         }
         K[d] = acc;
     }
-    const int nin = dir == 0 ? a.lp : N;
-    const int nout = dir == 0 ? N : a.lp;
+    const int nin = dir == 0 ? a.lp : a.nu;
+    const int nout = dir == 0 ? a.nu : a.lp;
     const double sR = dir == 0 ? (a.bcr == PSTD_NEUMANN ? 1.0 : -1.0)
                                : (a.bcr == PSTD_NEUMANN ? -1.0 : 1.0);
     std::vector<double> D((size_t)nout * nin);
     for (int i = 0; i < nout; ++i) {
         const int pos = dir == 0 ? i : i + a.lo;
         for (int j = 0; j < nin; ++j) {
+            // positions of stored input j in one period of the extension: itself
+            // and its reflection about the right wall (R2 - q, R2 - 1 - m) unless
+            // it lies on a wall
             int src[2];
             double sg[2];
             int nimg = 0;
@@ -283,10 +300,10 @@ std::vector<double> dense_operator64(const Axis& a, int dir, double scale) {
             } else if (dir == 0) {
                 const int q = j + a.lo;
                 src[nimg] = q; sg[nimg++] = 1.0;
-                if (q > 0 && q < N) { src[nimg] = 2 * N - q; sg[nimg++] = sR; }
+                if (q > 0 && 2 * q < a.R2) { src[nimg] = a.R2 - q; sg[nimg++] = sR; }
             } else {
                 src[nimg] = j; sg[nimg++] = 1.0;
-                src[nimg] = 2 * N - 1 - j; sg[nimg++] = sR;
+                if (2 * j + 1 < a.R2) { src[nimg] = a.R2 - 1 - j; sg[nimg++] = sR; }
             }
             double v = 0;
             for (int m = 0; m < nimg; ++m) {
@@ -421,11 +438,13 @@ bool kind_geo(const Axis& a, int kind, KindGeo& g) {
     const bool leftS = ppar == (a.bcl == PSTD_NEUMANN);
     g.sR = rightS ? 1.0f : -1.0f;
     if (half) {
+        // half-nodes m = 0..N-1; with a mid-cell right wall m = N-1 lies on it
         g.lo = 0;
-        g.len = a.N;
+        g.len = a.mid && !rightS ? a.N - 1 : a.N;
     } else {
+        // nodes up to N (wall node), or N - 1 before a mid-cell wall
         g.lo = leftS ? 0 : 1;
-        g.len = (rightS ? a.N : a.N - 1) - g.lo + 1;
+        g.len = (a.mid ? a.N - 1 : (rightS ? a.N : a.N - 1)) - g.lo + 1;
     }
     return g.len > 0;
 }
@@ -442,21 +461,9 @@ int out_kind(int op, int kind) {
 // e^{i k shift}; at the Nyquist bin of an even period only its real part,
 // which keeps real lines real (the bin the tables drop or pad with zero).
 std::complex<double> coeff_gen(const Axis& a, int n, bool deriv, double shift) {
-    const int N = a.N, L = a.L;
-    double kap;
+    const int L = a.L;
     bool nyquist = false;
-    if (a.periodic) {
-        const int nn = n < (L + 1) / 2 ? n : n - L;
-        kap = 2.0 * M_PI * nn / (L * a.dx);
-        nyquist = (L % 2 == 0 && n == L / 2);
-    } else if (!a.group2) {
-        const int nn = n <= N ? n : n - L;
-        kap = 2.0 * M_PI * nn / (L * a.dx);
-        nyquist = (n == N);
-    } else {
-        const int nn = n < N ? n : n - L;
-        kap = M_PI * (2.0 * nn + 1.0) / (L * a.dx);
-    }
+    const double kap = wavenumber(a, n, nyquist);
     std::complex<double> m = std::polar(1.0, kap * shift);
     if (deriv) m *= std::complex<double>(0.0, kap);
     if (nyquist) m = m.real();
@@ -511,10 +518,10 @@ std::vector<float> dense_operator_of(const Axis& a, const std::vector<std::compl
             } else if (!gi.half) {
                 const int q = j + gi.lo;
                 src[nimg] = q; sg[nimg++] = 1.0;
-                if (q > 0 && q < N) { src[nimg] = 2 * N - q; sg[nimg++] = gi.sR; }
+                if (q > 0 && 2 * q < a.R2) { src[nimg] = a.R2 - q; sg[nimg++] = gi.sR; }
             } else {
                 src[nimg] = j; sg[nimg++] = 1.0;
-                src[nimg] = 2 * N - 1 - j; sg[nimg++] = gi.sR;
+                if (2 * j + 1 < a.R2) { src[nimg] = a.R2 - 1 - j; sg[nimg++] = gi.sR; }
             }
             double v = 0;
             for (int m = 0; m < nimg; ++m) {
@@ -631,13 +638,22 @@ int build_axis(pstd_plan_s* P, int i) {
     a.dx = d.dx[i];
     a.bcl = d.bc[i][0];
     a.bcr = d.bc[i][1];
+    // a mid-cell right wall keeps its parity (Neumann / Dirichlet) in bcr
+    a.mid = a.bcr == PSTD_NEUMANN_MID || a.bcr == PSTD_DIRICHLET_MID;
+    if (a.mid) a.bcr = a.bcr == PSTD_NEUMANN_MID ? PSTD_NEUMANN : PSTD_DIRICHLET;
+    if (a.mid && P->opts.form != 0) return PSTD_EUNSUPPORTED;
     a.periodic = a.bcl == PSTD_PERIODIC;
-    // period of the extension: 2N (groups I, II) or N (periodic axis)
-    a.L = a.periodic ? a.N : 2 * a.N;
+    // period of the extension: 2N (groups I, II), 2N - 1 (groups III, IV:
+    // right wall at mid-cell) or N (periodic axis)
+    a.R2 = a.mid ? 2 * a.N - 1 : 2 * a.N;
+    a.L = a.periodic ? a.N : a.R2;
     a.group2 = !a.periodic && a.bcl != a.bcr;
     a.lo = a.bcl == PSTD_DIRICHLET ? 1 : 0;
-    const int hi = a.periodic ? a.N - 1 : (a.bcr == PSTD_DIRICHLET ? a.N - 1 : a.N);
+    const int hi = (a.periodic || a.mid) ? a.N - 1 : (a.bcr == PSTD_DIRICHLET ? a.N - 1 : a.N);
     a.lp = hi - a.lo + 1;
+    // velocity half-nodes: the one on a mid-cell wall is stored only where u
+    // is symmetric about it (Dirichlet)
+    a.nu = a.mid && a.bcr == PSTD_NEUMANN ? a.N - 1 : a.N;
     const bool fft_ok = radix_schedule(a.L, a.fft);
     a.kind = fft_ok ? 0 : (a.N <= kDenseMaxN ? 1 : 2);
     if (a.kind == 2) {
@@ -677,13 +693,14 @@ int build_axis(pstd_plan_s* P, int i) {
         std::memset(&op, 0, sizeof(op));
         op.kind = a.kind;
         op.N = a.N;
+        op.R2 = a.R2;
         op.L = a.L;
         op.group2 = a.group2;
         op.dir = dir;
         op.in_half = dir;
         op.out_half = 1 - dir;
-        op.nin = dir == 0 ? a.lp : a.N;
-        op.nout = dir == 0 ? a.N : a.lp;
+        op.nin = dir == 0 ? a.lp : a.nu;
+        op.nout = dir == 0 ? a.nu : a.lp;
         op.in_lo = a.lo;
         op.out_lo = a.lo;
         op.s_right = dir == 0 ? (a.bcr == PSTD_NEUMANN ? 1.0f : -1.0f)
@@ -724,7 +741,7 @@ int build_axis(pstd_plan_s* P, int i) {
     }
     a.nlines = nl;
     a.inner = inner;
-    a.rs = a.lp > a.N ? a.lp : a.N;
+    a.rs = a.lp > a.nu ? a.lp : a.nu;
     int G = 16;
     while (G > 2 && pstd::cta_smem_bytes(G, FL, a.rs) > kSmemBudget) G -= 2;
     if ((int64_t)G > nl) G = (int)nl;
@@ -969,21 +986,32 @@ int validate(const pstd_desc* d) {
     for (int i = 0; i < d->ndim; ++i) {
         if (d->ncells[i] < 1 || d->ncells[i] > (1 << 20)) return PSTD_EINVAL;
         if (!(d->dx[i] > 0) || !std::isfinite(d->dx[i])) return PSTD_EINVAL;
-        for (int s = 0; s < 2; ++s)
-            if (d->bc[i][s] != PSTD_NEUMANN && d->bc[i][s] != PSTD_DIRICHLET && d->bc[i][s] != PSTD_PERIODIC)
-                return PSTD_EINVAL;
-        if ((d->bc[i][0] == PSTD_PERIODIC) != (d->bc[i][1] == PSTD_PERIODIC)) return PSTD_EINVAL;
-        if (d->bc[i][0] == PSTD_PERIODIC && d->ncells[i] < 2) return PSTD_EINVAL;
-        if (d->ncells[i] == 1 && d->bc[i][0] == PSTD_DIRICHLET && d->bc[i][1] == PSTD_DIRICHLET)
+        const int l = d->bc[i][0], r = d->bc[i][1];
+        if (l != PSTD_NEUMANN && l != PSTD_DIRICHLET && l != PSTD_PERIODIC) return PSTD_EINVAL;
+        if (r != PSTD_NEUMANN && r != PSTD_DIRICHLET && r != PSTD_PERIODIC && r != PSTD_NEUMANN_MID &&
+            r != PSTD_DIRICHLET_MID)
             return PSTD_EINVAL;
+        if ((l == PSTD_PERIODIC) != (r == PSTD_PERIODIC)) return PSTD_EINVAL;
+        if (l == PSTD_PERIODIC && d->ncells[i] < 2) return PSTD_EINVAL;
+        if (d->ncells[i] == 1 && l == PSTD_DIRICHLET && r == PSTD_DIRICHLET) return PSTD_EINVAL;
+        if (d->ncells[i] < 2 && (r == PSTD_NEUMANN_MID || r == PSTD_DIRICHLET_MID)) return PSTD_EINVAL;
     }
     // leapfrog limit: c0 dt |k|_max / 2 <= 1 with the largest stored-mode
-    // wavenumber of each axis (NN keeps k = pi/dx; ND/DN pi(N-1/2)/L; DD pi(N-1)/L)
+    // wavenumber of each axis (NN keeps k = pi/dx; ND/DN pi(N-1/2)/L; DD pi(N-1)/L;
+    // mid-cell right wall, M = 2N - 1: same parity 2 pi (N-1) / (M dx), ND-mid
+    // pi / dx, DN-mid pi (M - 2) / (M dx))
     double k2 = 0;
     for (int i = 0; i < d->ndim; ++i) {
         const double N = (double)d->ncells[i], L = N * d->dx[i];
+        const int l = d->bc[i][0], r = d->bc[i][1];
         double kmax;
-        if (d->bc[i][0] == PSTD_PERIODIC) kmax = 2.0 * M_PI * std::floor(N / 2.0) / L;
+        if (r == PSTD_NEUMANN_MID || r == PSTD_DIRICHLET_MID) {
+            const double M = 2.0 * N - 1.0, dx = d->dx[i];
+            const bool same = (l == PSTD_NEUMANN) == (r == PSTD_NEUMANN_MID);
+            if (same) kmax = 2.0 * M_PI * (N - 1.0) / (M * dx);
+            else if (l == PSTD_NEUMANN) kmax = M_PI / dx;
+            else kmax = M_PI * (M - 2.0) / (M * dx);
+        } else if (l == PSTD_PERIODIC) kmax = 2.0 * M_PI * std::floor(N / 2.0) / L;
         else if (d->bc[i][0] == PSTD_NEUMANN && d->bc[i][1] == PSTD_NEUMANN) kmax = M_PI * N / L;
         else if (d->bc[i][0] != d->bc[i][1]) kmax = M_PI * (N - 0.5) / L;
         else kmax = M_PI * (N - 1.0) / L;
@@ -1330,14 +1358,16 @@ int pstd_plan_ex(const pstd_desc* desc, void* stream, const pstd_plan_opts* opts
         for (int j = 0; j < 3; ++j) P->shape[f][j] = 1;
     for (int i = 0; i < P->ndim; ++i) {
         const int64_t N = desc->ncells[i];
+        const int r = desc->bc[i][1];
+        const bool mid = r == PSTD_NEUMANN_MID || r == PSTD_DIRICHLET_MID;
         const int64_t lo = desc->bc[i][0] == PSTD_DIRICHLET ? 1 : 0;
-        const int64_t hi = desc->bc[i][0] == PSTD_PERIODIC ? N - 1
-                           : (desc->bc[i][1] == PSTD_DIRICHLET ? N - 1 : N);
+        const int64_t hi = (desc->bc[i][0] == PSTD_PERIODIC || mid) ? N - 1 : (r == PSTD_DIRICHLET ? N - 1 : N);
         P->shape[0][i] = hi - lo + 1;
     }
     for (int f = 1; f <= P->ndim; ++f) {
         for (int j = 0; j < P->ndim; ++j) P->shape[f][j] = P->shape[0][j];
-        P->shape[f][f - 1] = desc->ncells[f - 1];
+        // velocity half-nodes; N - 1 next to a Neumann mid-cell wall
+        P->shape[f][f - 1] = desc->ncells[f - 1] - (desc->bc[f - 1][1] == PSTD_NEUMANN_MID ? 1 : 0);
     }
     for (int i = 0; i < P->ndim && rc == PSTD_OK; ++i) rc = build_axis(P, i);
     if (rc == PSTD_OK && P->opts.form == 2) {

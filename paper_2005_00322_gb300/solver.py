@@ -18,11 +18,12 @@ _UINIT = {"halfstep": _abi.U_HALFSTEP, "as_given": _abi.U_AS_GIVEN}
 
 def stored_node_range(n: int, bc) -> tuple:
     """(first, last) stored pressure node of an axis: Dirichlet wall nodes are
-    dropped; a periodic axis stores nodes 0..N-1."""
+    dropped; a periodic axis stores nodes 0..N-1, and so does an axis whose
+    right wall is at mid-cell ("Nm" / "Dm", x = (N - 1/2) dx)."""
     if bc[0] in ("P", _abi.PERIODIC):
         return 0, n - 1
     lo = 1 if bc[0] in ("D", _abi.DIRICHLET) else 0
-    hi = n - 1 if bc[1] in ("D", _abi.DIRICHLET) else n
+    hi = n - 1 if bc[1] in ("D", _abi.DIRICHLET, "Nm", "Dm", _abi.NEUMANN_MID, _abi.DIRICHLET_MID) else n
     return lo, hi
 
 
@@ -30,7 +31,8 @@ class Solver:
     """A plan of the DTT-PSTD leapfrog on one GPU (see include/pstd.h).
 
     ncells: cells per axis (1 to 3 axes); dx: spacing (scalar or per axis);
-    bc: per axis a (left, right) pair of "N" / "D"; dt or cfl (dt = cfl dx / c0
+    bc: per axis a (left, right) pair of "N" / "D" / "P", the right wall also
+    "Nm" / "Dm" (at mid-cell, Table 1 groups III / IV); dt or cfl (dt = cfl dx / c0
     with the smallest dx); uinit: "halfstep" or "as_given".
     """
 
