@@ -455,9 +455,9 @@ def main():
     ap.add_argument("--leapfrog-steps", type=int, default=0, help="override the workload's step count")
     ap.add_argument("--persistent", action="store_true",
                     help="pstd_run as one cooperative kernel with grid barriers")
-    ap.add_argument("--form", default="fft", choices=["fft", "split", "tensor", "order2"],
-                    help="fft: spectral FFT route; split: FP16 hi/lo dense form (mma.sync); "
-                         "tensor: TF32 hi/lo dense form on tcgen05; order2: second-order "
+    ap.add_argument("--form", default="fft", choices=["fft", "split", "split-bf16", "tensor", "order2"],
+                    help="fft: spectral FFT route; split / split-bf16: FP16 / BF16 hi/lo dense form "
+                         "(mma.sync); tensor: TF32 hi/lo dense form on tcgen05; order2: second-order "
                          "pressure-only form on the FFT passes")
     ap.add_argument("--learned", action="store_true",
                     help="train and time the learned operator against 200 PSTD steps (prints its own line)")
@@ -565,10 +565,28 @@ def main():
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
                 "alg_bytes_per_launch": alg_bytes,
                 "launch_s": per_launch if single else None, "step_s": step_s}
+    if single and args.form in ("split", "split-bf16", "tensor"):
+        # dense split forms: tensor-bound GEMMs.  Per axis and step two GEMMs
+        # (N x lp and lp x N operators) over cells / lp lines, three split
+        # products each: 12 N x cells flops.  Form 2 launches two GEMMs per axis.
+        cells_p = int(np.prod(run.solver.shapes[0]))
+        flops_step = sum(12.0 * n * cells_p for n in w.ncells)
+        nl = w.ndim * (2 if args.form == "tensor" else 1)
+        sust = peaks.get("bf16_tflops_sustained", 1700.0)
+        tpeak = sust * (1.1 / 2.25) if args.form == "tensor" else sust
+        ach = flops_step / step_s / 1e12
+        roofline = {"bound": "tensor", "achieved": ach, "peak": tpeak, "unit": "TFLOP/s", "frac": ach / tpeak,
+                    "traffic": traffic,
+                    "kernel": "k_tc_gemm<1> (tcgen05 kind::tf32)" if args.form == "tensor"
+                    else "k_gemm_step (mma.sync m16n8k16 %s)" % ("bf16" if args.form == "split-bf16" else "f16"),
+                    "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained x 1.1/2.25 nominal tf32:bf16 "
+                                    "(of measured)") if args.form == "tensor" else
+                                   "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
+                    "alg_flops_per_launch": flops_step / nl, "launch_s": step_s / nl, "step_s": step_s}
 
     # end to end through the public API with host buffers
     h2d = sum(h.numel() * 4 for h in (run.host_in if single else [x for m in run.host_in for x in m]))
-    d2h = h2d
+    d2h = sum(h.numel() * 4 for h in (run.host_out if single else [x for m in run.host_out for x in m]))
     torch.cuda.synchronize()
     if dist:
         dist.barrier()

@@ -59,7 +59,7 @@ extern "C" {
  * (u is symmetric there), so u_axis has N - 1 (Neumann) or N entries along
  * its axis.  These axes run on the generic FFT route (3- and 5-smooth M),
  * the convolution route or the dense route; plans with a split form
- * (pstd_plan_opts.form 1, 2) reject them with PSTD_EUNSUPPORTED. */
+ * (pstd_plan_opts.form 1, 2, 3) reject them with PSTD_EUNSUPPORTED. */
 typedef enum {
     PSTD_NEUMANN = 0,
     PSTD_DIRICHLET = 1,
@@ -133,7 +133,9 @@ typedef struct {
      *    5th-generation tensor cores (tcgen05, kind::tf32): operator and field
      *    each split into TF32 hi + lo parts, Ah Bh + Ah Bl + Al Bh accumulated
      *    in FP32 in tensor memory (axes with N <= 1024); a bounded wait that
-     *    gives up is reported by pstd_sync as PSTD_ETIMEOUT. */
+     *    gives up is reported by pstd_sync as PSTD_ETIMEOUT;
+     * 3: form 1 with BF16 hi/lo operands (low parts scaled by 2^8, about 17
+     *    significant bits per entry instead of 22). */
     int form;
     /* 1: pstd_run is one cooperative kernel for all its steps, the CTAs
      * meeting at a bounded-wait grid barrier between axis passes (when every

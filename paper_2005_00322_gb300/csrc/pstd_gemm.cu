@@ -16,6 +16,11 @@
 // FP32 accumulate); A fragments come from a fragment-ordered copy of D in
 // global memory (one 16-byte load per lane), B fragments from the lines in
 // shared memory, [line][k] with a padded row.
+//
+// The same kernel runs with BF16 operands (pstd_plan_opts.form = 3): hi / lo
+// split with the low parts scaled by 2^8, so each entry keeps ~17 bits
+// (8 + 8 significant bits and the rounding of each) instead of ~22.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -26,20 +31,41 @@ namespace pstd {
 
 namespace {
 
-__device__ __forceinline__ void mma16816(float (&c)[4], const uint4& a, uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 "
-        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
-}
+// Operand type traits: FP16 (low parts x 2^11) or BF16 (low parts x 2^8).
+template <class T>
+struct Split;
+template <>
+struct Split<__half> {
+    static constexpr float kLo = 2048.0f;
+    __device__ static __half cvt(float x) { return __float2half_rn(x); }
+    __device__ static float back(__half h) { return __half2float(h); }
+    __device__ static void mma(float (&c)[4], const uint4& a, uint32_t b0, uint32_t b1) {
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 "
+            "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+            : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+            : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
+    }
+};
+template <>
+struct Split<__nv_bfloat16> {
+    static constexpr float kLo = 256.0f;
+    __device__ static __nv_bfloat16 cvt(float x) { return __float2bfloat16_rn(x); }
+    __device__ static float back(__nv_bfloat16 h) { return __bfloat162float(h); }
+    __device__ static void mma(float (&c)[4], const uint4& a, uint32_t b0, uint32_t b1) {
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+            "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+            : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+            : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
+    }
+};
 
-constexpr float kLoScale = 2048.0f;          // 2^11: low parts stored scaled
-
-__device__ __forceinline__ void split_store(__half* hi, __half* lo, float x) {
-    const __half h = __float2half_rn(x);
+template <class T>
+__device__ __forceinline__ void split_store(T* hi, T* lo, float x) {
+    const T h = Split<T>::cvt(x);
     *hi = h;
-    *lo = __float2half_rn((x - __half2float(h)) * kLoScale);
+    *lo = Split<T>::cvt((x - Split<T>::back(h)) * Split<T>::kLo);
 }
 
 // Element (line n, position k) of a tile of G lines.
@@ -71,10 +97,11 @@ __device__ __forceinline__ TileAddr tile_addr(const GemmAxis& A, int64_t block, 
     return t;
 }
 
-// Load G lines of `len` words into FP16 hi/lo rows of width `kp` (zero
-// padded), scaled per line by 1 / max|x|; smax[n] receives max|x| as bits.
+// Load G lines of `len` words into hi/lo rows of width `kp` (zero padded),
+// scaled per line by 1 / max|x|; smax[n] receives max|x| as bits.
+template <class T>
 __device__ void load_split(const float* f, const TileAddr& t, int len, int Gv, int G, int kp, int ldb,
-                           __half* bh, __half* bl, unsigned* smax) {
+                           T* bh, T* bl, unsigned* smax) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int total = G * kp;
     const bool contig = t.nstride != 1;
@@ -104,9 +131,10 @@ __device__ void load_split(const float* f, const TileAddr& t, int len, int Gv, i
 // tiles biases the result toward zero, a systematic error that would grow
 // into phase drift.  The 2^-11-scaled cross terms are too small for that to
 // matter.
+template <class T>
 __device__ __forceinline__ void gemm_tile(float (&acc)[8][4], float (&acc2)[8][4], const uint4* Ah,
                                           const uint4* Al, int mt,
-                                          int KT, const __half* bh, const __half* bl, int ldb, int ntiles,
+                                          int KT, const T* bh, const T* bl, int ldb, int ntiles,
                                           int lane) {
     const int gid = lane >> 2, tig = lane & 3;
     for (int kt = 0; kt < KT; ++kt) {
@@ -122,20 +150,22 @@ __device__ __forceinline__ void gemm_tile(float (&acc)[8][4], float (&acc2)[8][4
             const uint32_t bl0 = *(const uint32_t*)&bl[n * ldb + k];
             const uint32_t bl1 = *(const uint32_t*)&bl[n * ldb + k + 8];
             float t[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            mma16816(t, ah, bh0, bh1);
+            Split<T>::mma(t, ah, bh0, bh1);
             acc[nt][0] += t[0];
             acc[nt][1] += t[1];
             acc[nt][2] += t[2];
             acc[nt][3] += t[3];
-            mma16816(acc2[nt], ah, bl0, bl1);
-            mma16816(acc2[nt], al, bh0, bh1);
+            Split<T>::mma(acc2[nt], ah, bl0, bl1);
+            Split<T>::mma(acc2[nt], al, bh0, bh1);
         }
     }
 }
 
 }  // namespace
 
+template <class T>
 __global__ void __launch_bounds__(256) k_gemm_step(GemmStep a) {
+    constexpr float kLoScale = Split<T>::kLo;
     extern __shared__ float4 gsm4[];
     const GemmAxis& A = a.ax;
     const int G = A.G;
@@ -143,8 +173,8 @@ __global__ void __launch_bounds__(256) k_gemm_step(GemmStep a) {
     const int ld1 = kp1 + 8, ld2 = kp2 + 8;     // padded rows: conflict-free B loads
     const size_t rows = (size_t)G * (ld1 > ld2 ? ld1 : ld2);
     // [hi rows | lo rows] of GEMM 1's lines, later reused for GEMM 2's lines
-    __half* bh = (__half*)gsm4;
-    __half* bl = bh + rows;
+    T* bh = (T*)gsm4;
+    T* bl = bh + rows;
     float* un = (float*)(bl + rows);            // u_new, [G][N], FP32
     unsigned* smax1 = (unsigned*)(un + (size_t)G * A.N);
     unsigned* smax2 = smax1 + G;
@@ -187,7 +217,7 @@ __global__ void __launch_bounds__(256) k_gemm_step(GemmStep a) {
         }
     }
     __syncthreads();
-    // u_new rows -> FP16 hi / lo, scaled per line (over GEMM 1's rows)
+    // u_new rows -> hi / lo, scaled per line (over GEMM 1's rows)
     for (int idx = tid; idx < G * kp2; idx += blockDim.x) {
         const int n = idx / kp2, k = idx - n * kp2;
         float x = 0.0f;
@@ -223,13 +253,16 @@ __global__ void __launch_bounds__(256) k_gemm_step(GemmStep a) {
     }
 }
 
-cudaError_t launch_gemm_step(unsigned grid, size_t smem, cudaStream_t st, const GemmStep& a) {
-    k_gemm_step<<<grid, 256, smem, st>>>(a);
+cudaError_t launch_gemm_step(unsigned grid, size_t smem, cudaStream_t st, const GemmStep& a, bool bf16) {
+    if (bf16) k_gemm_step<__nv_bfloat16><<<grid, 256, smem, st>>>(a);
+    else k_gemm_step<__half><<<grid, 256, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t gemm_set_smem(int bytes) {
-    return cudaFuncSetAttribute(k_gemm_step, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_step<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_gemm_step<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 size_t gemm_smem_bytes(int G, int KT1, int KT2, int N) {

@@ -326,11 +326,26 @@ std::vector<float> dense_operator(const Axis& a, int dir, double scale) {
     return std::vector<float>(d.begin(), d.end());
 }
 
-// Fragment-ordered FP16 hi / lo copies of D / max|D| (rows m < M, cols k < K)
+// BF16 bits of a finite float, rounded to nearest even, and back.
+uint16_t bf16_bits(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+double bf16_value(uint16_t b) {
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// Fragment-ordered hi / lo copies of D / max|D| (rows m < M, cols k < K)
 // for mma m16n8k16: per (16-row tile, 16-column tile) 32 lanes x 4 words.
-// The low part is stored multiplied by 2^11 (see pstd_gemm.cu).
+// FP16 with the low part stored multiplied by 2^11, or BF16 (`bf16`) with
+// the low part multiplied by 2^8 (see pstd_gemm.cu).
 void gemm_fragments(const std::vector<double>& D, int M, int K, std::vector<uint4>& hi,
-                    std::vector<uint4>& lo, double& scale) {
+                    std::vector<uint4>& lo, double& scale, bool bf16) {
     double mx = 0;
     for (double v : D) mx = std::fabs(v) > mx ? std::fabs(v) : mx;
     scale = mx > 0 ? mx : 1.0;
@@ -339,6 +354,10 @@ void gemm_fragments(const std::vector<double>& D, int M, int K, std::vector<uint
     lo.assign(hi.size(), uint4{0, 0, 0, 0});
     auto el = [&](int m, int k, bool low) -> uint16_t {
         double x = (m < M && k < K) ? D[(size_t)m * K + k] / scale : 0.0;
+        if (bf16) {
+            const uint16_t h = bf16_bits((float)x);
+            return low ? bf16_bits((float)((x - bf16_value(h)) * 256.0)) : h;
+        }
         const __half h = __float2half_rn((float)x);
         __half r = h;
         if (low) r = __float2half_rn((float)((x - (double)__half2float(h)) * 2048.0));
@@ -907,12 +926,13 @@ int build_axis(pstd_plan_s* P, int i) {
     }
 
     // split-precision dense form
-    if (P->opts.form == 1) {
+    if (P->opts.form == 1 || P->opts.form == 3) {
         if (a.N > 1024) return PSTD_EUNSUPPORTED;
+        const bool bf16 = P->opts.form == 3;
         std::vector<uint4> h1, l1, h2, l2;
         double s1, s2;
-        gemm_fragments(dense_operator64(a, 0, scales[OP_STEP_P]), a.N, a.lp, h1, l1, s1);
-        gemm_fragments(dense_operator64(a, 1, scales[OP_STEP_U]), a.lp, a.N, h2, l2, s2);
+        gemm_fragments(dense_operator64(a, 0, scales[OP_STEP_P]), a.N, a.lp, h1, l1, s1, bf16);
+        gemm_fragments(dense_operator64(a, 1, scales[OP_STEP_U]), a.lp, a.N, h2, l2, s2, bf16);
         std::vector<uint4> all;
         all.insert(all.end(), h1.begin(), h1.end());
         all.insert(all.end(), l1.begin(), l1.end());
@@ -1093,14 +1113,14 @@ int launch_step(pstd_plan_s* P, float* p, float* const* u, int64_t* launches) {
             ++*launches;
             continue;
         }
-        if (P->opts.form == 1) {
+        if (P->opts.form == 1 || P->opts.form == 3) {
             pstd::GemmStep g;
             g.ax = A.gax;
             g.p = p;
             g.u = u[a];
             g.acc_in = (a == P->ndim - 1) ? p : P->d_S;
             g.acc_out = (a == 0) ? p : P->d_S;
-            CK(pstd::launch_gemm_step(A.ggrid, A.gsmem, P->stream, g));
+            CK(pstd::launch_gemm_step(A.ggrid, A.gsmem, P->stream, g, P->opts.form == 3));
             ++*launches;
             continue;
         }
@@ -1348,7 +1368,7 @@ int pstd_plan_ex(const pstd_desc* desc, void* stream, const pstd_plan_opts* opts
     if (!P) return PSTD_ENOMEM;
     P->desc = *desc;
     if (opts) P->opts = *opts;
-    if (P->opts.form < 0 || P->opts.form > 2) {
+    if (P->opts.form < 0 || P->opts.form > 3) {
         delete P;
         return PSTD_EINVAL;
     }
@@ -1385,7 +1405,7 @@ int pstd_plan_ex(const pstd_desc* desc, void* stream, const pstd_plan_opts* opts
         for (int i = 0; i < P->ndim; ++i) mx = P->ax[i].smem > mx ? P->ax[i].smem : mx;
         cudaError_t e = pstd::set_max_smem((int)mx);
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaFuncSetAttribute");
-        if (rc == PSTD_OK && P->opts.form == 1) {
+        if (rc == PSTD_OK && (P->opts.form == 1 || P->opts.form == 3)) {
             int dev = 0, optin = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

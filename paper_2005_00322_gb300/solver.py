@@ -36,6 +36,10 @@ class Solver:
     with the smallest dx); uinit: "halfstep" or "as_given".
     """
 
+    # derivative forms (pstd_plan_opts.form): FFT passes, FP16 / BF16 split
+    # dense GEMMs on mma.sync, TF32 split dense GEMMs on tcgen05
+    FORMS = {"fft": 0, "split": 1, "tensor": 2, "split-bf16": 3}
+
     def __init__(self, ncells, dx, bc, c0=1500.0, rho0=1000.0, dt=None, cfl=None,
                  uinit="halfstep", device=None, stream=None, schedule=None, form="fft",
                  persistent=False, spin_limit=0, withhold_arrivals=0):
@@ -56,8 +60,8 @@ class Solver:
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
         opts = None
-        if form not in ("fft", "split", "tensor"):
-            raise ValueError("form is 'fft', 'split' or 'tensor'")
+        if form not in self.FORMS:
+            raise ValueError("form is one of " + ", ".join(repr(f) for f in self.FORMS))
         if schedule is not None or form != "fft" or persistent or withhold_arrivals:
             # schedule: per axis (variant, seqs_per_cta), None entries automatic
             opts = _abi.PstdPlanOpts()
@@ -65,7 +69,7 @@ class Solver:
                 v, q = (schedule[i] if schedule and i < len(schedule) and schedule[i] else (None, None))
                 opts.variant[i] = -1 if v is None else int(v)
                 opts.seqs_per_cta[i] = -1 if q is None else int(q)
-            opts.form = {"fft": 0, "split": 1, "tensor": 2}[form]
+            opts.form = self.FORMS[form]
             opts.persistent = 1 if persistent else 0
             opts.spin_limit = int(spin_limit)
             opts.withhold_arrivals = int(withhold_arrivals)
