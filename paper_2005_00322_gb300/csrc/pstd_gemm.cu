@@ -137,9 +137,17 @@ __device__ __forceinline__ void gemm_tile(float (&acc)[8][4], float (&acc2)[8][4
                                           int KT, const T* bh, const T* bl, int ldb, int ntiles,
                                           int lane) {
     const int gid = lane >> 2, tig = lane & 3;
+    // the operator fragments of k tile kt + 1 are loaded while the MMAs of
+    // tile kt run, so that the L2 latency overlaps tensor-core work (a
+    // distance of two tiles measured no faster)
+    uint4 ah = __ldg(&Ah[(size_t)mt * KT * 32 + lane]);
+    uint4 al = __ldg(&Al[(size_t)mt * KT * 32 + lane]);
     for (int kt = 0; kt < KT; ++kt) {
-        const uint4 ah = __ldg(&Ah[((size_t)mt * KT + kt) * 32 + lane]);
-        const uint4 al = __ldg(&Al[((size_t)mt * KT + kt) * 32 + lane]);
+        uint4 ah_next = ah, al_next = al;
+        if (kt + 1 < KT) {
+            ah_next = __ldg(&Ah[((size_t)mt * KT + kt + 1) * 32 + lane]);
+            al_next = __ldg(&Al[((size_t)mt * KT + kt + 1) * 32 + lane]);
+        }
 #pragma unroll
         for (int nt = 0; nt < 8; ++nt) {
             if (nt >= ntiles) break;
@@ -158,6 +166,8 @@ __device__ __forceinline__ void gemm_tile(float (&acc)[8][4], float (&acc2)[8][4
             Split<T>::mma(acc2[nt], ah, bl0, bl1);
             Split<T>::mma(acc2[nt], al, bh0, bh1);
         }
+        ah = ah_next;
+        al = al_next;
     }
 }
 
