@@ -878,6 +878,7 @@ int build_axis(pstd_plan_s* P, int i) {
             w.G = 2 * w.seqs;
             a.wgeo.grid = (unsigned)((nseq + w.seqs - 1) / w.seqs);
             a.wgeo.smem = (size_t)w.seqs * pstd::wseq_words(a.L) * sizeof(float2);
+            a.wgeo.smem += pstd::wk::contig_stage_floats(w) * sizeof(float);  // staged slots and accumulator
             a.wgeo.smem += (wt.size() + 4 * (size_t)a.L) * sizeof(float2);   // staged tables
         } else {
             const int64_t outer = a.nlines / a.inner;

@@ -384,13 +384,20 @@ PSTD_HD void update_and_inverse(float2 (&v)[S::E], const float2 (&w)[S::E], int 
 }
 
 // ---- contiguous layout ------------------------------------------------------
+// Shared memory of a contiguous step pass beyond its FFT buffers: each
+// sequence's two velocity-spectrum lines and two accumulator lines, staged
+// by the lean form (floats).
+PSTD_HD size_t contig_stage_floats(const WAxis& A) { return (size_t)A.seqs * (2 * A.N + 2 * A.lp); }
+
 template <class S>
 PSTD_HD void step_contig(const WStep& a, int64_t block, float2* smem, int tid, int nthr) {
     constexpr int T = S::T, E = S::E;
-    // Lean form (the 3-D lengths, L <= 768): nothing is prefetched across the forward
-    // FFT, so that the pass fits 128 registers and 4 CTAs per SM; the 2-D
-    // length 1024 is latency-bound and prefetches the slots, the symmetry
-    // factors and the accumulator with the tables.
+    // Lean form (the 3-D lengths, L <= 768): nothing is held in registers
+    // across the forward FFT, so that the pass fits 128 registers and 4 CTAs
+    // per SM; instead the spectrum slots and the accumulator are copied into
+    // shared memory (cp.async) while the forward FFT runs.  The 2-D length
+    // 1024 is latency-bound and prefetches the slots, the symmetry factors and
+    // the accumulator into registers with the tables.
     constexpr bool lean = S::V >= 1 && S::L <= 768;
     int sq, t;
     lane_of<S>(tid, sq, t);
@@ -432,6 +439,20 @@ PSTD_HD void step_contig(const WStep& a, int64_t block, float2* smem, int tid, i
     }
     async_wait_all();
     PSTD_SYNCCTA();
+    // lean form: this sequence's spectrum lines [a | b] and accumulator lines
+    // [a | b], copied now and read after the forward FFT
+    float* su = (float*)(bufs + (size_t)A.seqs * wf::seq_words<S::L>()) + (size_t)sq * (2 * N + 2 * lp);
+    float* sa = su + 2 * N;
+    if constexpr (lean) {
+        for (int i = t; i < N; i += T) {
+            if (va) async_copy4(&su[i], &ua[i]);
+            if (vbu) async_copy4(&su[N + i], &ub[i]);
+        }
+        for (int i = t; i < lp; i += T) {
+            if (va) async_copy4(&sa[i], &ia[i]);
+            if (vb) async_copy4(&sa[lp + i], &ib[i]);
+        }
+    }
     if constexpr (!lean) {
         // staged tables are readable from here on: non-owner bins from their slot
 #pragma unroll
@@ -447,10 +468,13 @@ PSTD_HD void step_contig(const WStep& a, int64_t block, float2* smem, int tid, i
     load_p_ext<S>(v, t, A, tab, [&](int i) { return make_float2(va ? pa[i] : 0.0f, vb ? pb[i] : 0.0f); });
     fft<S, false>(v, t, sm, tab);
     if constexpr (lean) {
-        load_spectrum<S>(w, t, A, tab, slot);
-        seq_sync<S>();   // every lane has read its slots before any owner writes
+        async_wait_all();
+        seq_sync<S>();   // every lane's copies are visible to the sequence
+        load_spectrum<S>(w, t, A, tab,
+                         [&](int s) { return make_float2(va ? su[s] : 0.0f, vbu ? su[N + s] : 0.0f); });
     }
-    // (prefetched form: the forward FFT's exchange barriers ordered the reads
+    // (the slots are read from the staged copy (lean form) or were prefetched
+    // before the forward FFT, whose exchange barriers ordered those reads
     // before the owner writes; a one-lane sequence has no other reader)
     update_and_inverse<S>(v, w, t, sm, A, tab, [&](int s, float2 x) {
         if (va) ua[s] = x.x;
@@ -462,7 +486,7 @@ PSTD_HD void step_contig(const WStep& a, int64_t block, float2* smem, int tid, i
     for (int e = 0; e < E; ++e) {
         const int i = t + T * e - A.lo;
         if (i >= 0 && i < lp) {
-            const float2 c = lean ? acc(e) : ao[e];
+            const float2 c = lean ? make_float2(va ? sa[i] : 0.0f, vb ? sa[lp + i] : 0.0f) : ao[e];
             if (va) oa[i] = c.x + v[e].x;
             if (vb) ob[i] = c.y + v[e].y;
         }
