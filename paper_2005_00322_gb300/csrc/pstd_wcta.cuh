@@ -622,11 +622,27 @@ PSTD_HD int log2_pow2(int G) {
     return s;
 }
 
+// Item idx of a tile is (position idx >> log2 G, line idx & (G-1)), so
+// consecutive threads cover the G adjacent lines of one position.  When the
+// CTA's thread count is a multiple of G (every schedule with two or more
+// lanes per sequence) each thread keeps one line and walks the positions with
+// fixed increments; otherwise (one lane per sequence, G > threads) the items
+// are enumerated directly.
 PSTD_HD void tile_load(const float* f, int len, const WAxis& A, int64_t o, int64_t i0, int Gv,
                        float* raw, int tid, int nthr) {
     const int rs = row_stride(len);
     const int gs = log2_pow2(A.G), gm = A.G - 1;
     const float* base = f + o * (int64_t)len * A.inner + i0;
+    if ((nthr & gm) == 0) {
+        const int g = tid & gm, step = nthr >> gs;
+        if (g >= Gv) return;
+        int pos = tid >> gs;
+        const float* src = base + (int64_t)pos * A.inner + g;
+        float* dst = raw + g * rs + pos;
+        const int64_t gstep = (int64_t)step * A.inner;
+        for (; pos < len; pos += step, src += gstep, dst += step) async_copy4(dst, src);
+        return;
+    }
     const int total = len << gs;
     for (int idx = tid; idx < total; idx += nthr) {
         const int pos = idx >> gs, g = idx & gm;
@@ -639,6 +655,16 @@ PSTD_HD void tile_store(float* f, int len, const WAxis& A, int64_t o, int64_t i0
     const int rs = row_stride(len);
     const int gs = log2_pow2(A.G), gm = A.G - 1;
     float* base = f + o * (int64_t)len * A.inner + i0;
+    if ((nthr & gm) == 0) {
+        const int g = tid & gm, step = nthr >> gs;
+        if (g >= Gv) return;
+        int pos = tid >> gs;
+        float* dst = base + (int64_t)pos * A.inner + g;
+        const float* src = raw + g * rs + pos;
+        const int64_t gstep = (int64_t)step * A.inner;
+        for (; pos < len; pos += step, dst += gstep, src += step) *dst = *src;
+        return;
+    }
     const int total = len << gs;
     for (int idx = tid; idx < total; idx += nthr) {
         const int pos = idx >> gs, g = idx & gm;
