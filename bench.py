@@ -1,6 +1,7 @@
 """Benchmark of the DTT-PSTD hot path: grid-point updates per second.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+                [--form fft|split|split-bf16|tensor|order2] [--persistent]
 python bench.py --learned [--learned-iters I]
 
 One bench step is one full configured simulation: the initial fields are
