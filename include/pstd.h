@@ -20,6 +20,9 @@
  *     a Neumann left wall and at node 1 for a Dirichlet one.
  *   - Velocity u_i lives on the N_i half-nodes (m + 1/2) dx_i along axis i and
  *     on the stored pressure nodes along every other axis.
+ *   - An axis whose right wall is at mid-cell (PSTD_NEUMANN_MID,
+ *     PSTD_DIRICHLET_MID below) stores the pressure nodes up to N_i - 1 and
+ *     N_i - 1 (Neumann) or N_i (Dirichlet) velocity half-nodes.
  *   pstd_field_shape() returns these shapes.
  *
  * Ownership: the caller allocates and owns every field buffer (device
