@@ -561,8 +561,10 @@ def main():
     achieved = alg_bytes / per_launch / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_wgrad dir 4 (second-order axis pass)" if args.form == "order2"
-                else "k_wstep (fused axis pass)",
+                "kernel": ("k_wgrad dir 4 (second-order axis pass)" if args.form == "order2"
+                           else "k_wstep (fused axis pass)") if single
+                else "every member's axis passes (k_wstep register passes, k_step generic / convolution "
+                     "passes), concurrent graph branches",
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
                 "alg_bytes_per_launch": alg_bytes,
                 "launch_s": per_launch if single else None, "step_s": step_s}
