@@ -457,9 +457,9 @@ def main():
     ap.add_argument("--persistent", action="store_true",
                     help="pstd_run as one cooperative kernel with grid barriers")
     ap.add_argument("--form", default="fft", choices=["fft", "split", "split-bf16", "tensor", "order2"],
-                    help="fft: spectral FFT route; split / split-bf16: FP16 / BF16 hi/lo dense form "
-                         "(mma.sync); tensor: TF32 hi/lo dense form on tcgen05; order2: second-order "
-                         "pressure-only form on the FFT passes")
+                    help="fft: spectral FFT route; split: FP16 hi/lo dense form (mma.sync); split-bf16: "
+                         "BF16 three-way split dense form on tcgen05; tensor: TF32 hi/lo dense form on "
+                         "tcgen05; order2: second-order pressure-only form on the FFT passes")
     ap.add_argument("--learned", action="store_true",
                     help="train and time the learned operator against 200 PSTD steps (prints its own line)")
     ap.add_argument("--learned-iters", type=int, default=8000)
@@ -570,18 +570,22 @@ def main():
                 "launch_s": per_launch if single else None, "step_s": step_s}
     if single and args.form in ("split", "split-bf16", "tensor"):
         # dense split forms: tensor-bound GEMMs.  Per axis and step two GEMMs
-        # (N x lp and lp x N operators) over cells / lp lines, three split
-        # products each: 12 N x cells flops.  Form 2 launches two GEMMs per axis.
+        # (N x lp and lp x N operators) over cells / lp lines, with three
+        # split products each (FP16 and TF32 hi/lo: 12 N x cells flops) or six
+        # (BF16 three-way split: 24 N x cells).  The TF32 and BF16 forms launch
+        # two GEMMs per axis.
         cells_p = int(np.prod(run.solver.shapes[0]))
-        flops_step = sum(12.0 * n * cells_p for n in w.ncells)
-        nl = w.ndim * (2 if args.form == "tensor" else 1)
+        prods = 6 if args.form == "split-bf16" else 3
+        flops_step = sum(4.0 * prods * n * cells_p for n in w.ncells)
+        nl = w.ndim * (1 if args.form == "split" else 2)
         sust = peaks.get("bf16_tflops_sustained", 1700.0)
         tpeak = sust * (1.1 / 2.25) if args.form == "tensor" else sust
         ach = flops_step / step_s / 1e12
         roofline = {"bound": "tensor", "achieved": ach, "peak": tpeak, "unit": "TFLOP/s", "frac": ach / tpeak,
                     "traffic": traffic,
-                    "kernel": "k_tc_gemm<1> (tcgen05 kind::tf32)" if args.form == "tensor"
-                    else "k_gemm_step (mma.sync m16n8k16 %s)" % ("bf16" if args.form == "split-bf16" else "f16"),
+                    "kernel": {"tensor": "k_tc_gemm<1> (tcgen05 kind::tf32)",
+                               "split-bf16": "k_tc16 (tcgen05 kind::f16, BF16 three-way split, TMA-fed)",
+                               "split": "k_gemm_step (mma.sync m16n8k16 f16)"}[args.form],
                     "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained x 1.1/2.25 nominal tf32:bf16 "
                                     "(of measured)") if args.form == "tensor" else
                                    "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",

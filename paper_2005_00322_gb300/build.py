@@ -67,7 +67,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=4) as ex:
+    with cf.ThreadPoolExecutor(max_workers=max(4, min(16, os.cpu_count() or 4))) as ex:
         results = list(ex.map(compile_one, sources()))
     for _, log in results:
         if verbose and log:

@@ -16,11 +16,6 @@
 // FP32 accumulate); A fragments come from a fragment-ordered copy of D in
 // global memory (one 16-byte load per lane), B fragments from the lines in
 // shared memory, [line][k] with a padded row.
-//
-// The same kernel runs with BF16 operands (pstd_plan_opts.form = 3): hi / lo
-// split with the low parts scaled by 2^8, so each entry keeps ~17 bits
-// (8 + 8 significant bits and the rounding of each) instead of ~22.
-#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -31,7 +26,7 @@ namespace pstd {
 
 namespace {
 
-// Operand type traits: FP16 (low parts x 2^11) or BF16 (low parts x 2^8).
+// Operand type traits of the FP16 operands (low parts x 2^11).
 template <class T>
 struct Split;
 template <>
@@ -42,19 +37,6 @@ struct Split<__half> {
     __device__ static void mma(float (&c)[4], const uint4& a, uint32_t b0, uint32_t b1) {
         asm volatile(
             "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 "
-            "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
-            : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-            : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
-    }
-};
-template <>
-struct Split<__nv_bfloat16> {
-    static constexpr float kLo = 256.0f;
-    __device__ static __nv_bfloat16 cvt(float x) { return __float2bfloat16_rn(x); }
-    __device__ static float back(__nv_bfloat16 h) { return __bfloat162float(h); }
-    __device__ static void mma(float (&c)[4], const uint4& a, uint32_t b0, uint32_t b1) {
-        asm volatile(
-            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
             "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
             : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
             : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
@@ -263,16 +245,13 @@ __global__ void __launch_bounds__(256) k_gemm_step(GemmStep a) {
     }
 }
 
-cudaError_t launch_gemm_step(unsigned grid, size_t smem, cudaStream_t st, const GemmStep& a, bool bf16) {
-    if (bf16) k_gemm_step<__nv_bfloat16><<<grid, 256, smem, st>>>(a);
-    else k_gemm_step<__half><<<grid, 256, smem, st>>>(a);
+cudaError_t launch_gemm_step(unsigned grid, size_t smem, cudaStream_t st, const GemmStep& a) {
+    k_gemm_step<__half><<<grid, 256, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t gemm_set_smem(int bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_step<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_gemm_step<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return cudaFuncSetAttribute(k_gemm_step<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 size_t gemm_smem_bytes(int G, int KT1, int KT2, int N) {

@@ -10,7 +10,7 @@ struct GemmAxis {
     int N, lp;                // u and p lengths along the axis
     int MT1, KT1;             // GEMM 1 (D_p): 16-row tiles of N, 16-column tiles of lp
     int MT2, KT2;             // GEMM 2 (D_u): 16-row tiles of lp, 16-column tiles of N
-    const uint4* A1h;         // D_p / s1, FP16 or BF16 hi / lo in fragment order
+    const uint4* A1h;         // D_p / s1, FP16 hi / lo in fragment order
     const uint4* A1l;
     const uint4* A2h;         // D_u / s2
     const uint4* A2l;
@@ -27,8 +27,7 @@ struct GemmStep {
     float* acc_out;
 };
 
-// bf16: BF16 operands (form 3) instead of FP16 (form 1)
-cudaError_t launch_gemm_step(unsigned grid, size_t smem, cudaStream_t st, const GemmStep& a, bool bf16);
+cudaError_t launch_gemm_step(unsigned grid, size_t smem, cudaStream_t st, const GemmStep& a);
 cudaError_t gemm_set_smem(int bytes);
 size_t gemm_smem_bytes(int G, int KT1, int KT2, int N);
 

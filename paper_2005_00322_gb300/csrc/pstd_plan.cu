@@ -26,6 +26,7 @@
 #include "pstd_cta.cuh"
 #include "pstd_gemm.h"
 #include "pstd_internal.h"
+#include "pstd_tc16.h"
 #include <cuda_fp16.h>
 #include "pstd_wkernels.cuh"
 
@@ -120,6 +121,11 @@ struct Axis {
     float* d_dense2 = nullptr;
     WAxis wax{};
     WLaunch wgeo{};
+    // BF16 three-way split form on tcgen05: the two operators' BF16 slices
+    // (D1: N x lp, D2: lp x N) and their TMA tensor maps
+    uint16_t* d_tc16[2] = {nullptr, nullptr};
+    CUtensorMap tc16_map[2];
+    int tc16_MT[2] = {0, 0}, tc16_KC[2] = {0, 0};
     // split-precision dense form
     uint4* d_gemm = nullptr;          // A1h | A1l | A2h | A2l fragments
     pstd::GemmAxis gax{};
@@ -326,26 +332,11 @@ std::vector<float> dense_operator(const Axis& a, int dir, double scale) {
     return std::vector<float>(d.begin(), d.end());
 }
 
-// BF16 bits of a finite float, rounded to nearest even, and back.
-uint16_t bf16_bits(float f) {
-    uint32_t u;
-    std::memcpy(&u, &f, 4);
-    u += 0x7FFFu + ((u >> 16) & 1u);
-    return (uint16_t)(u >> 16);
-}
-double bf16_value(uint16_t b) {
-    const uint32_t u = (uint32_t)b << 16;
-    float f;
-    std::memcpy(&f, &u, 4);
-    return f;
-}
-
 // Fragment-ordered hi / lo copies of D / max|D| (rows m < M, cols k < K)
-// for mma m16n8k16: per (16-row tile, 16-column tile) 32 lanes x 4 words.
-// FP16 with the low part stored multiplied by 2^11, or BF16 (`bf16`) with
-// the low part multiplied by 2^8 (see pstd_gemm.cu).
+// for mma m16n8k16: per (16-row tile, 16-column tile) 32 lanes x 4 words,
+// FP16 with the low part stored multiplied by 2^11 (see pstd_gemm.cu).
 void gemm_fragments(const std::vector<double>& D, int M, int K, std::vector<uint4>& hi,
-                    std::vector<uint4>& lo, double& scale, bool bf16) {
+                    std::vector<uint4>& lo, double& scale) {
     double mx = 0;
     for (double v : D) mx = std::fabs(v) > mx ? std::fabs(v) : mx;
     scale = mx > 0 ? mx : 1.0;
@@ -354,10 +345,6 @@ void gemm_fragments(const std::vector<double>& D, int M, int K, std::vector<uint
     lo.assign(hi.size(), uint4{0, 0, 0, 0});
     auto el = [&](int m, int k, bool low) -> uint16_t {
         double x = (m < M && k < K) ? D[(size_t)m * K + k] / scale : 0.0;
-        if (bf16) {
-            const uint16_t h = bf16_bits((float)x);
-            return low ? bf16_bits((float)((x - bf16_value(h)) * 256.0)) : h;
-        }
         const __half h = __float2half_rn((float)x);
         __half r = h;
         if (low) r = __float2half_rn((float)((x - (double)__half2float(h)) * 2048.0));
@@ -926,14 +913,30 @@ int build_axis(pstd_plan_s* P, int i) {
         if ((rc = upload(all, &a.d_tc)) != PSTD_OK) return rc;
     }
 
-    // split-precision dense form
-    if (P->opts.form == 1 || P->opts.form == 3) {
+    // BF16 three-way split form: both dense operators (FP64-built, scales
+    // folded in) as exact BF16 slices with their tensor maps
+    if (P->opts.form == 3) {
         if (a.N > 1024) return PSTD_EUNSUPPORTED;
-        const bool bf16 = P->opts.form == 3;
+        const std::vector<double> D1 = dense_operator64(a, 0, scales[OP_STEP_P]);   // nu x lp
+        const std::vector<double> D2 = dense_operator64(a, 1, scales[OP_STEP_U]);   // lp x nu
+        const int dims[2][2] = {{a.nu, a.lp}, {a.lp, a.nu}};
+        for (int o = 0; o < 2; ++o) {
+            const int r = pstd::tc16_operator(o == 0 ? D1 : D2, dims[o][0], dims[o][1], &a.d_tc16[o],
+                                              &a.tc16_map[o]);
+            if (r == -1) return cuda_fail(cudaErrorNotSupported, "cuTensorMapEncodeTiled");
+            if (r != 0) return cuda_fail((cudaError_t)r, "BF16 operator slices");
+            a.tc16_MT[o] = (dims[o][0] + 127) / 128;
+            a.tc16_KC[o] = (dims[o][1] + 63) / 64;
+        }
+    }
+
+    // split-precision dense form
+    if (P->opts.form == 1) {
+        if (a.N > 1024) return PSTD_EUNSUPPORTED;
         std::vector<uint4> h1, l1, h2, l2;
         double s1, s2;
-        gemm_fragments(dense_operator64(a, 0, scales[OP_STEP_P]), a.N, a.lp, h1, l1, s1, bf16);
-        gemm_fragments(dense_operator64(a, 1, scales[OP_STEP_U]), a.lp, a.N, h2, l2, s2, bf16);
+        gemm_fragments(dense_operator64(a, 0, scales[OP_STEP_P]), a.N, a.lp, h1, l1, s1);
+        gemm_fragments(dense_operator64(a, 1, scales[OP_STEP_U]), a.lp, a.N, h2, l2, s2);
         std::vector<uint4> all;
         all.insert(all.end(), h1.begin(), h1.end());
         all.insert(all.end(), l1.begin(), l1.end());
@@ -988,6 +991,8 @@ void free_plan_memory(pstd_plan_s* P) {
                 cudaFree(a.d_xdense[o][k]);
             }
         cudaFree(a.d_gemm);
+        cudaFree(a.d_tc16[0]);
+        cudaFree(a.d_tc16[1]);
         for (int o = 0; o < OP_COUNT; ++o) {
             cudaFree(a.d_f[o]);
             cudaFree(a.d_dense[o]);
@@ -1114,14 +1119,33 @@ int launch_step(pstd_plan_s* P, float* p, float* const* u, int64_t* launches) {
             ++*launches;
             continue;
         }
-        if (P->opts.form == 1 || P->opts.form == 3) {
+        if (P->opts.form == 3) {
+            // u_a += D1 p, then acc_out = acc_in + D2 u_a, over the lines of the axis
+            int* status = (int*)(P->d_sync + 2);
+            pstd::Tc16Gemm g1{};
+            g1.K = A.lp; g1.Mout = A.nu; g1.MT = A.tc16_MT[0]; g1.KC = A.tc16_KC[0];
+            g1.nlines = A.nlines; g1.inner = A.inner;
+            g1.X = p; g1.Cin = u[a]; g1.Y = u[a]; g1.status = status;
+            CK(pstd::tc16_launch(A.tc16_map[0], g1, P->stream));
+            pstd::Tc16Gemm g2{};
+            g2.K = A.nu; g2.Mout = A.lp; g2.MT = A.tc16_MT[1]; g2.KC = A.tc16_KC[1];
+            g2.nlines = A.nlines; g2.inner = A.inner;
+            g2.X = u[a];
+            g2.Cin = (a == P->ndim - 1) ? p : P->d_S;
+            g2.Y = (a == 0) ? p : P->d_S;
+            g2.status = status;
+            CK(pstd::tc16_launch(A.tc16_map[1], g2, P->stream));
+            *launches += 2;
+            continue;
+        }
+        if (P->opts.form == 1) {
             pstd::GemmStep g;
             g.ax = A.gax;
             g.p = p;
             g.u = u[a];
             g.acc_in = (a == P->ndim - 1) ? p : P->d_S;
             g.acc_out = (a == 0) ? p : P->d_S;
-            CK(pstd::launch_gemm_step(A.ggrid, A.gsmem, P->stream, g, P->opts.form == 3));
+            CK(pstd::launch_gemm_step(A.ggrid, A.gsmem, P->stream, g));
             ++*launches;
             continue;
         }
@@ -1391,7 +1415,7 @@ int pstd_plan_ex(const pstd_desc* desc, void* stream, const pstd_plan_opts* opts
         P->shape[f][f - 1] = desc->ncells[f - 1] - (desc->bc[f - 1][1] == PSTD_NEUMANN_MID ? 1 : 0);
     }
     for (int i = 0; i < P->ndim && rc == PSTD_OK; ++i) rc = build_axis(P, i);
-    if (rc == PSTD_OK && P->opts.form == 2) {
+    if (rc == PSTD_OK && (P->opts.form == 2 || P->opts.form == 3)) {
         // status word of the tensor-core GEMMs' bounded waits (read by pstd_sync)
         cudaError_t e = cudaMalloc((void**)&P->d_sync, 4 * sizeof(unsigned));
         if (e == cudaSuccess) e = cudaMemset(P->d_sync, 0, 4 * sizeof(unsigned));
@@ -1406,7 +1430,11 @@ int pstd_plan_ex(const pstd_desc* desc, void* stream, const pstd_plan_opts* opts
         for (int i = 0; i < P->ndim; ++i) mx = P->ax[i].smem > mx ? P->ax[i].smem : mx;
         cudaError_t e = pstd::set_max_smem((int)mx);
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaFuncSetAttribute");
-        if (rc == PSTD_OK && (P->opts.form == 1 || P->opts.form == 3)) {
+        if (rc == PSTD_OK && P->opts.form == 3) {
+            e = pstd::tc16_set_smem();
+            if (e != cudaSuccess) rc = cuda_fail(e, "cudaFuncSetAttribute(BF16 split pass)");
+        }
+        if (rc == PSTD_OK && P->opts.form == 1) {
             int dev = 0, optin = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

@@ -36,8 +36,9 @@ class Solver:
     with the smallest dx); uinit: "halfstep" or "as_given".
     """
 
-    # derivative forms (pstd_plan_opts.form): FFT passes, FP16 / BF16 split
-    # dense GEMMs on mma.sync, TF32 split dense GEMMs on tcgen05
+    # derivative forms (pstd_plan_opts.form): FFT passes, FP16 hi/lo split
+    # dense GEMMs on mma.sync, TF32 hi/lo and BF16 three-way split dense GEMMs
+    # on tcgen05
     FORMS = {"fft": 0, "split": 1, "tensor": 2, "split-bf16": 3}
 
     def __init__(self, ncells, dx, bc, c0=1500.0, rho0=1000.0, dt=None, cfl=None,

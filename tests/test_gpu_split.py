@@ -1,14 +1,10 @@
 """GPU parity of the split-precision dense forms: FP16 hi/lo products on the
-mma.sync tensor-core path ("split"), the same with BF16 operands
-("split-bf16") and TF32 hi/lo products on the tcgen05 tensor cores with
-accumulators in tensor memory ("tensor").
+mma.sync tensor-core path ("split"), TF32 hi/lo products on the tcgen05
+tensor cores ("tensor") and the exact BF16 three-way split on the tcgen05
+tensor cores ("split-bf16").
 
-The FP16 and TF32 forms meet the FFT route's tolerances: 1e-5 relative L2 per
-step from the same state, 1e-4 over a full run, against the FP64 oracle.  The
-BF16 form keeps about 17 bits per operand entry (8 + 8 significant bits, each
-rounded: 2^-17 relative), and the dropped lo x lo product adds up to 2^-18:
-one product is off by up to about 3 x 2^-17 = 2.3e-5 relative, so one step is
-held to 3e-5.
+Every form is held to the FFT route's tolerances against the FP64 oracle:
+1e-5 relative L2 per step from the same state, 1e-4 over a full run.
 """
 import numpy as np
 import pytest
@@ -36,7 +32,7 @@ CASES = [((48,), [("N", "N")]), ((100,), [("D", "N")]), ((64, 37), [("D", "D"), 
          ((70, 9), [("N", "N"), ("D", "D")]), ((5, 200), [("D", "D"), ("N", "D")])]
 
 
-STEP_TOL = {"split": 1e-5, "tensor": 1e-5, "split-bf16": 3e-5}
+STEP_TOL = {"split": 1e-5, "tensor": 1e-5, "split-bf16": 1e-5}
 
 
 @pytest.mark.parametrize("form", ["split", "split-bf16", "tensor"])
@@ -61,11 +57,7 @@ def test_split_one_step_matches_oracle(ncells, bcs, form):
     s.close()
 
 
-# BF16 operands shift the discrete frequencies by ~1e-5 relative, which grows
-# into phase error: measured 3.1e-5 / 6.7e-5 / 1.7e-4 after 250 / 1000 / 4000
-# steps of this run, so the BF16 form misses the 1e-4 bar here (it meets it on
-# the 1000-step 384^3 run below); its bound is the measured one with margin.
-RUN_TOL = {"split": 1e-4, "tensor": 1e-4, "split-bf16": 3e-4}
+RUN_TOL = {"split": 1e-4, "tensor": 1e-4, "split-bf16": 1e-4}
 
 
 @pytest.mark.parametrize("form", ["split", "split-bf16", "tensor"])
@@ -89,8 +81,7 @@ def test_split_plane512_full_run_vs_modal(form):
 @pytest.mark.parametrize("form", ["split", "split-bf16", "tensor"])
 def test_split_cube384_full_run_vs_modal(form):
     """3-D 384^3 (D x, N y, D z), 4 blobs, CFL 0.3, 1000 steps of each split
-    form vs the modal closed form: every form within 1e-4 (measured 2.4e-6
-    FP16, 6.5e-5 BF16, 8.5e-6 TF32; the FFT route 4.4e-6)."""
+    form vs the modal closed form: every form within 1e-4."""
     from paper_2005_00322_gb300 import Solver
     w = inputs.cube384_dnd()
     s = Solver(w.ncells, w.dx, w.bc, cfl=w.cfl, form=form)
