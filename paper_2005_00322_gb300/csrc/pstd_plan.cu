@@ -926,7 +926,7 @@ int build_axis(pstd_plan_s* P, int i) {
             if (r == -1) return cuda_fail(cudaErrorNotSupported, "cuTensorMapEncodeTiled");
             if (r != 0) return cuda_fail((cudaError_t)r, "BF16 operator slices");
             a.tc16_MT[o] = (dims[o][0] + 127) / 128;
-            a.tc16_KC[o] = (dims[o][1] + 63) / 64;
+            a.tc16_KC[o] = pstd::tc16_chunks(dims[o][1]);
         }
     }
 
