@@ -519,21 +519,32 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc16(const __grid_constant__ CUt
             if (lane == 0) mbar_arrive(bar(ACC_EMPTY));
             group_sync(1);
             // Y = Cin + sum, coalesced: contiguous axes walk lines (the rows of
-            // the tile are consecutive words), strided axes walk rows
+            // the tile are consecutive words), strided axes walk rows.  Each
+            // warp takes every fourth line (row) in batches of 16, so that 64
+            // loads of Cin per lane are in flight at once.
+            constexpr int WB = 16;
             if (g.inner == 1) {
-                for (int ll = ew; ll < NL; ll += 4) {
-                    const int64_t lg = l0 + ll;
-                    if (lg >= g.nlines) break;
-                    float cin[4];
+                for (int b0 = 0; b0 < NL / 4; b0 += WB) {
+                    float cin[WB][4];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int m = mt * BM + 32 * i + lane;
-                        cin[i] = m < g.Mout ? g.Cin[lg * g.Mout + m] : 0.0f;
+                    for (int u = 0; u < WB; ++u) {
+                        const int64_t lg = l0 + ew + 4 * (b0 + u);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int m = mt * BM + 32 * i + lane;
+                            cin[u][i] = (lg < g.nlines && m < g.Mout) ? g.Cin[lg * g.Mout + m] : 0.0f;
+                        }
                     }
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int m = mt * BM + 32 * i + lane;
-                        if (m < g.Mout) g.Y[lg * g.Mout + m] = cin[i] + OB[ll * OB_LD + 32 * i + lane];
+                    for (int u = 0; u < WB; ++u) {
+                        const int ll = ew + 4 * (b0 + u);
+                        const int64_t lg = l0 + ll;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int m = mt * BM + 32 * i + lane;
+                            if (lg < g.nlines && m < g.Mout)
+                                g.Y[lg * g.Mout + m] = cin[u][i] + OB[ll * OB_LD + 32 * i + lane];
+                        }
                     }
                 }
             } else {
@@ -545,15 +556,24 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc16(const __grid_constant__ CUt
                     ov[i] = lg < g.nlines;
                     ob[i] = ov[i] ? (lg / g.inner) * (int64_t)g.Mout * g.inner + (lg % g.inner) : 0;
                 }
-                for (int rr = ew; rr < BM; rr += 4) {
-                    const int m = mt * BM + rr;
-                    if (m >= g.Mout) break;
-                    float cin[4];
+                for (int b0 = 0; b0 < BM / 4; b0 += WB) {
+                    float cin[WB][4];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) cin[i] = ov[i] ? g.Cin[ob[i] + (int64_t)m * g.inner] : 0.0f;
+                    for (int u = 0; u < WB; ++u) {
+                        const int m = mt * BM + ew + 4 * (b0 + u);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        if (ov[i]) g.Y[ob[i] + (int64_t)m * g.inner] = cin[i] + OB[rr * OB_LD + 32 * i + lane];
+                        for (int i = 0; i < 4; ++i)
+                            cin[u][i] = (ov[i] && m < g.Mout) ? g.Cin[ob[i] + (int64_t)m * g.inner] : 0.0f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < WB; ++u) {
+                        const int rr = ew + 4 * (b0 + u);
+                        const int m = mt * BM + rr;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            if (ov[i] && m < g.Mout)
+                                g.Y[ob[i] + (int64_t)m * g.inner] = cin[u][i] + OB[rr * OB_LD + 32 * i + lane];
+                    }
                 }
             }
             group_sync(1);      // the output tile is read before the next one overwrites it
