@@ -204,6 +204,72 @@ def rank_max(x: float, dist, device) -> float:
     return float(t.item())
 
 
+def modal_rel_l2(w, solver, p_final) -> float:
+    """Relative L2 of the final pressure of one full run of ``w`` against the
+    FP64 separable modal solution (the CPU leg: calls oracle/)."""
+    from oracle import modal, pstd
+    od = pstd.Desc(w.ncells, (w.dx,), w.bc, c0=w.c0, rho0=w.rho0, dt=solver.dt)
+    facs = [[term[i][pstd.p_nodes(n, b)] for i, (n, b) in enumerate(zip(w.ncells, w.bc))]
+            for term in w.factors()]
+    ref = modal.separable_modal_pressure(od, facs, w.steps)
+    got = np.asarray(p_final, np.float64)
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+
+def energy_drift(run) -> dict:
+    """|E^n - E^0| / E^0 over one full run of the workload, the energies formed
+    in FP64 on the GPU (pstd_energy) from p^n, u^{n-1/2} and u^{n+1/2}."""
+    import torch
+    s = run.solver
+    p, us = run.p, run.us
+    p.copy_(run.p0)
+    for u in us:
+        u.zero_()
+    s.init_velocity(p, us)
+
+    def energy_now():
+        pn, uprev = p.clone(), [u.clone() for u in us]
+        s.step(p, us)
+        return s.energy(pn, uprev, us)
+    e0 = energy_now()
+    s.run(p, us, run.w.steps - 2)
+    e1 = energy_now()
+    torch.cuda.synchronize()
+    return {"value": abs(e1 - e0) / e0, "steps": run.w.steps, "e0": e0,
+            "how": "pstd_energy (FP64 on the GPU) after step 1 and after the last step"}
+
+
+def hbm_case(peak: float, name: str = "cube256_ddnndd") -> dict:
+    """The HBM-bound configuration: one plain FP32 256^3 grid (DD / NN / DD),
+    axis passes timed from graph-replayed runs of 32 and 96 steps (events on
+    the plan's stream; the 268 MB state exceeds L2)."""
+    import torch
+    w = WORKLOADS[name]()
+    r = SingleRunner(w)
+    r.p.copy_(r.p0)
+    r.solver.init_velocity(r.p, r.us)
+    st = r.stream
+
+    def run_time(n):
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(st)
+        r.leapfrog(n)
+        a1.record(st)
+        a1.synchronize()
+        return a0.elapsed_time(a1) / 1e3
+    run_time(32)
+    step_s = (run_time(96) - run_time(32)) / 64
+    alg_step = 2 * (w.ndim + 1) * 4 * cells(w)
+    per_launch = step_s / w.ndim
+    ach = alg_step / w.ndim / per_launch / 1e9
+    r.close()
+    return {"workload": name, "ms_per_step": step_s * 1e3, "updates_per_s": cells(w) / step_s,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "kernel": "k_wstep (fused axis pass)", "alg_bytes_per_launch": alg_step / w.ndim,
+                         "launch_s": per_launch}}
+
+
 def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
     """Units processed by all ranks divided by the slowest rank's time."""
     return units_per_rank * world / seconds_max
@@ -604,7 +670,24 @@ def main():
     te = rank_max(time.perf_counter() - t0, dist, "cuda")
     e2e = {"value": updates / te, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    # accuracy of the benchmarked run: the final pressure of the last e2e run
+    # (a full configured run from p0) against the FP64 modal solution, and the
+    # FP64 energy drift over one full run (single coupled-leapfrog grids)
+    acc = None
+    drift = None
+    if single and rank == 0:
+        p_fin = run.host_out[0].numpy().copy()
+        if not (args.form == "order2"):
+            drift = energy_drift(run)
+    hbm = None
+    if rank == 0 and not (single and w0.ncells == WORKLOADS["cube256_ddnndd"]().ncells and args.form == "fft"):
+        hbm = hbm_case(peak)
+
     cpu = None
+    if rank == 0 and world == 1 and single and steps_per == w0.steps:
+        acc = {"value": modal_rel_l2(w0, run.solver, p_fin), "unit": "rel L2 of p",
+               "against": "FP64 separable modal solution (oracle/modal.py)",
+               "steps": steps_per, "bar": 1e-4}
     if rank == 0 and world == 1:
         wc = w0 if single or isinstance(w, list) else inputs.cube256(bc=(("N", "N"),) * 3)
         o2 = args.form == "order2" and single
@@ -631,6 +714,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": cfg, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk.summary(), "gpu_launches": launches,
+            "rel_l2_vs_fp64": acc, "energy_drift_fp64": drift, "hbm_case": hbm,
         }
         print(json.dumps(line), flush=True)
     run.close()

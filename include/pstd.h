@@ -108,9 +108,13 @@ typedef struct pstd_plan_s pstd_plan_t;
  * coefficients -(dt/rho0) i k e^{+ik dx/2} / M and -(dt rho0 c0^2) i k
  * e^{-ik dx/2} / M of the symmetric-periodic extension of each axis, Table 1)
  * and rounds them once to FP32; allocates them and one scratch accumulator of
- * the pressure shape (ndim >= 2) on the device.  Axes whose 2 N_i factors
- * into 2, 3 and 5 use shared-memory FFT kernels; other axes with N_i <= 256
- * use a dense operator matrix; larger other axes return PSTD_EUNSUPPORTED.
+ * the pressure shape (ndim >= 2) on the device.  Routes per axis, by the
+ * period M of its extension: the register-FFT passes for M in {2..1024
+ * powers of two, 96, 192, 384, 768}; shared-memory Stockham FFT passes for
+ * other M with prime factors 2, 3 and 5 only; for any other M, a dense
+ * operator matrix when N_i <= 64, else a (skew-)circular convolution of
+ * length M evaluated as a power-of-two linear convolution (FFT length up to
+ * 8192, i.e. M up to 4096; longer such axes return PSTD_EUNSUPPORTED).
  * `stream` is a cudaStream_t (NULL = legacy default stream).
  * Errors: PSTD_EINVAL (ndim, N_i, dx, c0, rho0, dt, bc or uinit out of
  * range; N_i = 1 with DD walls has no pressure node), PSTD_EUNSTABLE,
@@ -137,8 +141,13 @@ typedef struct {
      *    each split into TF32 hi + lo parts, Ah Bh + Ah Bl + Al Bh accumulated
      *    in FP32 in tensor memory (axes with N <= 1024); a bounded wait that
      *    gives up is reported by pstd_sync as PSTD_ETIMEOUT;
-     * 3: form 1 with BF16 hi/lo operands (low parts scaled by 2^8, about 17
-     *    significant bits per entry instead of 22). */
+     * 3: BF16 split form on the 5th-generation tensor cores (tcgen05,
+ *    kind::f16): the same dense operators, operator and field cut into three
+ *    BF16 slices each on per-(row, 32-wide k block) and per-(line, block)
+ *    power-of-two grids, so that each block's main product sums exactly in
+ *    tensor memory; FP32 accumulation; operator slices fed by TMA (axes with
+ *    N <= 1024); a bounded wait that gives up is reported by pstd_sync as
+ *    PSTD_ETIMEOUT. */
     int form;
     /* 1: pstd_run is one cooperative kernel for all its steps, the CTAs
      * meeting at a bounded-wait grid barrier between axis passes (when every
@@ -196,6 +205,22 @@ int pstd_step(pstd_plan_t* plan, float* p, float* const* u);
  * a tail shorter than the block is launched directly.
  * Errors: PSTD_EINVAL, PSTD_ECUDA. */
 int pstd_run(pstd_plan_t* plan, float* p, float* const* u, int64_t nsteps);
+
+/* Discrete energy of the leapfrog state in FP64, computed on the GPU:
+ *     E^n = sum_j w_j (p_j^n)^2 / (2 rho0 c0^2)
+ *         + (rho0 / 2) sum_i sum_j w_ij u_{i,j}^{n-1/2} u_{i,j}^{n+1/2},
+ * the quantity the staggered leapfrog of Eq. (dtt_pstd_solution) conserves
+ * (Section 4.1's scheme; a reading, the paper states no energy).  Weights are
+ * tensor products over axes: 1/2 on a stored pressure node on a Neumann
+ * wall, 1/2 on the velocity half-node a Dirichlet mid-cell wall passes
+ * through, 1 elsewhere.  `p` holds p^n, `u_prev` / `u_next` host arrays of
+ * ndim device pointers to u^{n-1/2} and u^{n+1/2} (physical velocity, as
+ * pstd_step / pstd_run leave it; layout of pstd_field_shape).  Each product is
+ * formed in FP64 and summed in FP64 in a fixed order.  Enqueued on the plan's
+ * stream after its earlier work; waits for the result and writes it to the
+ * host double *energy.  The plan allocates a small FP64 scratch on first use.
+ * Errors: PSTD_EINVAL (NULL argument), PSTD_ENOMEM, PSTD_ECUDA. */
+int pstd_energy(pstd_plan_t* plan, const float* p, float* const* u_prev, float* const* u_next, double* energy);
 
 /* Synchronise the plan's stream; reports device-side errors, and
  * PSTD_ETIMEOUT once (then clears it) if a bounded wait of a persistent run
@@ -349,14 +374,19 @@ int pstd_reflection_combos(const pstd_desc* tmpl, const double* refl, pstd_desc*
  * default stream).  The scratch accumulator and the coefficient tables live in
  * fixed file-scope device arrays (16 MiB + 384 KiB, held on every GPU that
  * loads the library until the process exits); each call recomputes the tables
- * in FP64 on the device.  The first call on a device also resolves those
- * arrays' device addresses (with that device current); make that first call
- * before any stream capture.  All calls share the arrays: calls whose work
- * overlaps on the GPU race, so serialise them (one stream, one host thread).
- * Only axes whose 2 N_i factors into 2, 3 and 5 are supported, with
- * 2 N_i <= PSTD_NOALLOC_MAX_FFT and at most PSTD_NOALLOC_MAX_POINTS pressure
- * points; larger or other sizes return PSTD_EUNSUPPORTED before any device
- * work.  u^{-1/2} must already be in u (see pstd_init_velocity).
+ * in FP64 on the device, and looks the arrays' device addresses up on the
+ * current device (a host-side query).  Under CUDA's lazy module loading the
+ * arrays are committed when the first call on a device loads the module: that
+ * first call is the one that takes device memory, so make it once at start-up
+ * (and before any stream capture); later calls take none.  All calls share
+ * the arrays: calls whose work overlaps on the GPU race, so serialise them
+ * (one stream, one host thread).
+ * Only Neumann and Dirichlet walls at the grid nodes are supported (periodic
+ * axes and mid-cell walls return PSTD_EUNSUPPORTED), on axes whose 2 N_i
+ * factors into 2, 3 and 5, with 2 N_i <= PSTD_NOALLOC_MAX_FFT and at most
+ * PSTD_NOALLOC_MAX_POINTS pressure points; larger or other sizes return
+ * PSTD_EUNSUPPORTED before any device work.  u^{-1/2} must already be in u
+ * (see pstd_init_velocity).
  * Errors: PSTD_EINVAL, PSTD_EUNSTABLE, PSTD_EUNSUPPORTED, PSTD_ECUDA. */
 int pstd_step_noalloc(const pstd_desc* desc, float* p, float* const* u, int64_t nsteps,
                       void* stream);

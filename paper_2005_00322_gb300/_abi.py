@@ -34,6 +34,7 @@ SIGNATURES = {
     "pstd_run": (c_int, [c_void_p, c_void_p, POINTER(c_void_p), c_int64]),
     "pstd_init_prev": (c_int, [c_void_p, c_void_p, c_void_p]),
     "pstd_run2": (c_int, [c_void_p, c_void_p, c_void_p, c_int64]),
+    "pstd_energy": (c_int, [c_void_p, c_void_p, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_double)]),
     "pstd_sync": (c_int, [c_void_p]),
     "pstd_free": (c_int, [c_void_p]),
     "pstd_strerror": (c_char_p, [c_int]),

@@ -17,15 +17,17 @@
 //                     every call.
 //
 // Host code may not use these names as device addresses (on the host they are
-// stand-ins, not device pointers), so the first call on each device looks
-// their addresses up with cudaGetSymbolAddress while that device is current
-// and caches them.  Every call shares the arrays and leaves them holding its
-// own tables and partial sums; two calls whose work overlaps on the GPU (two
-// streams, or two host threads) race on them.
+// stand-ins, not device pointers), so every call looks their addresses up with
+// cudaGetSymbolAddress on the current device, a host-side query that
+// allocates nothing; nothing is cached, so a device reset or a new primary
+// context (which may load the module at new addresses) cannot leave a stale
+// pointer behind.  Under lazy module loading the arrays are committed when the
+// first call on a device loads the module.  Every call shares the arrays and
+// leaves them holding its own tables and partial sums; two calls whose work
+// overlaps on the GPU (two streams, or two host threads) race on them.
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 
 #include "../../include/pstd.h"
 #include "pstd_cta.cuh"
@@ -38,42 +40,24 @@ cudaError_t set_max_smem(int bytes);
 namespace {
 
 constexpr int kMaxFft = PSTD_NOALLOC_MAX_FFT;
-constexpr int kMaxDevices = 64;
 constexpr size_t kSmemBudget = 100 * 1024;
 
 static __device__ __align__(256) float g_noalloc_acc[PSTD_NOALLOC_MAX_POINTS];
 static __device__ __align__(256) float2 g_noalloc_tables[3][4][kMaxFft];
 
-struct DeviceSlots {
-    bool ready = false;
-    float* acc = nullptr;
-    float2* tables = nullptr;
-};
-DeviceSlots g_slots[kMaxDevices];
-std::mutex g_slots_mu;
-
-// Per-device set-up: resolve the arrays' device addresses (device current).
-cudaError_t slots_for_current_device(DeviceSlots** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+// Device addresses of the arrays on the current device, and the step
+// kernels' shared-memory limit (both host-side calls that allocate nothing).
+cudaError_t resolve_arrays(float** acc, float2** tables) {
+    void* a = nullptr;
+    void* t = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_acc);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_slots_mu);
-    DeviceSlots& s = g_slots[dev];
-    if (!s.ready) {
-        void* acc = nullptr;
-        void* tab = nullptr;
-        e = cudaGetSymbolAddress(&acc, g_noalloc_acc);
-        if (e != cudaSuccess) return e;
-        e = cudaGetSymbolAddress(&tab, g_noalloc_tables);
-        if (e != cudaSuccess) return e;
-        e = pstd::set_max_smem((int)kSmemBudget);
-        if (e != cudaSuccess) return e;
-        s.acc = (float*)acc;
-        s.tables = (float2*)tab;
-        s.ready = true;
-    }
-    *out = &s;
+    e = cudaGetSymbolAddress(&t, g_noalloc_tables);
+    if (e != cudaSuccess) return e;
+    e = pstd::set_max_smem((int)kSmemBudget);
+    if (e != cudaSuccess) return e;
+    *acc = (float*)a;
+    *tables = (float2*)t;
     return cudaSuccess;
 }
 
@@ -147,8 +131,14 @@ extern "C" int pstd_step_noalloc(const pstd_desc* d, float* p, float* const* u, 
     for (int i = 0; i < d->ndim; ++i) {
         const int64_t N = d->ncells[i];
         if (!u[i] || N < 1 || !(d->dx[i] > 0)) return PSTD_EINVAL;
-        for (int s = 0; s < 2; ++s)
-            if (d->bc[i][s] != PSTD_NEUMANN && d->bc[i][s] != PSTD_DIRICHLET) return PSTD_EINVAL;
+        for (int s = 0; s < 2; ++s) {
+            const int b = d->bc[i][s];
+            // valid wall types this call has no schedule for: periodic axes and
+            // mid-cell right walls
+            if (b == PSTD_PERIODIC || (s == 1 && (b == PSTD_NEUMANN_MID || b == PSTD_DIRICHLET_MID)))
+                return PSTD_EUNSUPPORTED;
+            if (b != PSTD_NEUMANN && b != PSTD_DIRICHLET) return PSTD_EINVAL;
+        }
         const int64_t lo = d->bc[i][0] == PSTD_DIRICHLET ? 1 : 0;
         const int64_t hi = d->bc[i][1] == PSTD_DIRICHLET ? N - 1 : N;
         if (hi < lo) return PSTD_EINVAL;
@@ -170,8 +160,9 @@ extern "C" int pstd_step_noalloc(const pstd_desc* d, float* p, float* const* u, 
             return PSTD_EUNSUPPORTED;
     }
 
-    DeviceSlots* slots = nullptr;
-    if (slots_for_current_device(&slots) != cudaSuccess) return PSTD_ECUDA;
+    float* acc = nullptr;
+    float2* tables = nullptr;
+    if (resolve_arrays(&acc, &tables) != cudaSuccess) return PSTD_ECUDA;
     cudaStream_t st = (cudaStream_t)stream;
 
     pstd::StepArgs args[3];
@@ -182,7 +173,7 @@ extern "C" int pstd_step_noalloc(const pstd_desc* d, float* p, float* const* u, 
         const int bcl = d->bc[i][0], bcr = d->bc[i][1];
         const int lo = bcl == PSTD_DIRICHLET ? 1 : 0;
         const int lp = (int)pshape[i];
-        float2* tab = slots->tables + (size_t)i * 4 * kMaxFft;
+        float2* tab = tables + (size_t)i * 4 * kMaxFft;
         AxisSpec spec{N, L, bcl != bcr, d->dx[i], -d->dt / d->rho0, -d->dt * d->rho0 * d->c0 * d->c0};
         k_noalloc_tables<<<(L + 255) / 256, 256, 0, st>>>(spec, tab);
         if (cudaGetLastError() != cudaSuccess) return PSTD_ECUDA;
@@ -229,8 +220,8 @@ extern "C" int pstd_step_noalloc(const pstd_desc* d, float* p, float* const* u, 
         args[i].rs = rs;
         args[i].p = p;
         args[i].u = u[i];
-        args[i].acc_in = (i == d->ndim - 1) ? p : slots->acc;
-        args[i].acc_out = (i == 0) ? p : slots->acc;
+        args[i].acc_in = (i == d->ndim - 1) ? p : acc;
+        args[i].acc_out = (i == 0) ? p : acc;
         grids[i] = (unsigned)((nl + G - 1) / G);
     }
     for (int64_t s = 0; s < nsteps; ++s) {

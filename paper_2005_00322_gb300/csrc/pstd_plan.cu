@@ -24,6 +24,7 @@
 
 #include "../../include/pstd.h"
 #include "pstd_cta.cuh"
+#include "pstd_energy.h"
 #include "pstd_gemm.h"
 #include "pstd_internal.h"
 #include "pstd_tc16.h"
@@ -224,6 +225,7 @@ struct pstd_plan_s {
     int64_t shape[4][3] = {};
     Axis ax[3];
     float* d_S = nullptr;
+    double* d_energy = nullptr;       // pstd_energy's FP64 partial sums, on first use
     int64_t last_launches = 0;
     GraphEntry graphs[kGraphCache];
     uint64_t stamp = 0;
@@ -999,6 +1001,7 @@ void free_plan_memory(pstd_plan_s* P) {
         }
     }
     cudaFree(P->d_S);
+    cudaFree(P->d_energy);
     cudaFree(P->d_sync);
     for (auto& g : P->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -1681,6 +1684,42 @@ int pstd_run2(pstd_plan_t* P, float* p, float* p_prev, int64_t nsteps) {
     CK(pstd::launch_k_axpby(n, 1.0f, p, -1.0f, q, P->stream));   // p^{n-1} = p^n - q
     ++conv;
     P->last_launches += conv;
+    return PSTD_OK;
+}
+
+int pstd_energy(pstd_plan_t* P, const float* p, float* const* u_prev, float* const* u_next, double* energy) {
+    if (!P || !p || !u_prev || !u_next || !energy) return PSTD_EINVAL;
+    const int d = P->ndim;
+    for (int i = 0; i < d; ++i)
+        if (!u_prev[i] || !u_next[i]) return PSTD_EINVAL;
+    constexpr int kBlocks = 304;
+    if (!P->d_energy) {
+        cudaError_t e = cudaMalloc((void**)&P->d_energy, (4 * kBlocks + 1) * sizeof(double));
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? PSTD_ENOMEM : cuda_fail(e, "cudaMalloc(energy)");
+    }
+    pstd::EnergyField f[4];
+    pstd::EnergyScales sc{};
+    for (int fi = 0; fi <= d; ++fi) {
+        f[fi].a = fi == 0 ? p : u_prev[fi - 1];
+        f[fi].b = fi == 0 ? p : u_next[fi - 1];
+        for (int j = 0; j < 3; ++j) f[fi].n[j] = P->shape[fi][j];
+        f[fi].first_half = f[fi].last_half = 0;
+        for (int a = 0; a < d; ++a) {
+            const int l = P->desc.bc[a][0], r = P->desc.bc[a][1];
+            if (fi == a + 1) {
+                // the velocity's own axis: the half-node on a Dirichlet mid-cell wall
+                if (r == PSTD_DIRICHLET_MID) f[fi].last_half |= 1 << a;
+            } else {
+                // pressure nodes on Neumann walls (a mid-cell wall has no node)
+                if (l == PSTD_NEUMANN) f[fi].first_half |= 1 << a;
+                if (r == PSTD_NEUMANN) f[fi].last_half |= 1 << a;
+            }
+        }
+        sc.s[fi] = fi == 0 ? 1.0 / (2.0 * P->desc.rho0 * P->desc.c0 * P->desc.c0) : 0.5 * P->desc.rho0;
+    }
+    CK(pstd::energy_launch(f, d + 1, sc, kBlocks, P->d_energy, P->stream));
+    CK(cudaMemcpyAsync(energy, P->d_energy + 4 * kBlocks, sizeof(double), cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
     return PSTD_OK;
 }
 

@@ -216,6 +216,15 @@ class Solver:
         _abi.check(self.lib, self.lib.pstd_run2(self._h, a, b, int(nsteps)), "pstd_run2")
         self._leave()
 
+    def energy(self, p, u_prev, u_next):
+        """FP64 discrete energy E^n of (p^n, u^{n-1/2}, u^{n+1/2}), computed on
+        the GPU (pstd_energy)."""
+        a, prev, nxt = self._t(p, 0, "p"), self._us(u_prev), self._us(u_next)
+        out = ctypes.c_double()
+        self._enter()
+        _abi.check(self.lib, self.lib.pstd_energy(self._h, a, prev, nxt, ctypes.byref(out)), "pstd_energy")
+        return out.value
+
     def sync(self):
         _abi.check(self.lib, self.lib.pstd_sync(self._h), "pstd_sync")
 

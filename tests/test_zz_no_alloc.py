@@ -52,13 +52,18 @@ def test_noalloc_matches_planned_path(ncells, bcs, steps):
     stream = torch.cuda.current_stream()
     ptrs = (ctypes.c_void_p * 3)(*[u.data_ptr() for u in ub])
 
-    for n in steps:                      # two calls in a row on the same buffers
+    for call, n in enumerate(steps):     # two calls in a row on the same buffers
         solver.run(pa, ua, n)
         solver.sync()
+        free_before = torch.cuda.mem_get_info()[0]
         rc = lib.pstd_step_noalloc(ctypes.byref(desc), ctypes.c_void_p(pb.data_ptr()), ptrs,
                                    n, ctypes.c_void_p(stream.cuda_stream))
         assert rc == 0, _abi.ERRORS.get(rc, rc)
         torch.cuda.synchronize()
+        if call > 0:
+            # a call after the first takes no device memory (the first may have
+            # committed the file-scope arrays when it loaded the module)
+            assert torch.cuda.mem_get_info()[0] == free_before
         assert rel_l2(pb, pa) < 1e-5
         for a, b in zip(ua, ub):
             assert rel_l2(b, a) < 1e-5
@@ -80,3 +85,8 @@ def test_noalloc_rejects_sizes_beyond_capacity():
     # 2N = 14 has a factor 7: no FFT schedule
     odd = _abi.make_desc((7,), DX, [("N", "N")], 1500.0, 1000.0, 0.1 * DX / 1500.0)
     assert lib.pstd_step_noalloc(ctypes.byref(odd), ctypes.c_void_p(1), ptrs, 1, None) == -6
+    # valid wall types without a schedule here: periodic axes, mid-cell walls
+    per = _abi.make_desc((64,), DX, [("P", "P")], 1500.0, 1000.0, 0.1 * DX / 1500.0)
+    assert lib.pstd_step_noalloc(ctypes.byref(per), ctypes.c_void_p(1), ptrs, 1, None) == -6
+    mid = _abi.make_desc((64,), DX, [("D", "Nm")], 1500.0, 1000.0, 0.1 * DX / 1500.0)
+    assert lib.pstd_step_noalloc(ctypes.byref(mid), ctypes.c_void_p(1), ptrs, 1, None) == -6
