@@ -419,12 +419,18 @@ LEARNED_METRIC = "learned-operator 200-step pressure predictions/s (128x128 NN/D
 def learned_main(args) -> None:
     """--learned: the spectral neural operator against the solver it replaces.
 
-    Trains the network (4 layers, 32 channels, 16 modes per axis) on PSTD
-    answers for seeded smooth initial pressures, checks it on a held-out set
-    against PSTD (the solver is the judge: fallback tolerance 1e-2 relative
-    L2), and times batched inference (256 samples per call, device-resident,
-    L2 flushed between timed calls) against batched PSTD runs of the same
-    200 steps (64 members per graph launch).
+    The configured workload: a 128^2 box, Neumann walls on x and Dirichlet on y,
+    200 steps at CFL 0.3; inputs of 1-6 Gaussian blobs of sigma U[2, 8] dx
+    (inputs.sno_initial_pressures); 20k training samples (seed 1), 1k test
+    samples (seed 2) and 512 held-out samples (seed 3) that set the gate.  The
+    network (4 layers, 32 channels, 16 modes per axis) trains on PSTD answers.
+    The solver is the judge: requests whose content above the 16th mode is too
+    large for the network (gate set on the held-out set at tolerance 1e-2
+    relative L2) are answered by PSTD.  Reported: the network's error on the
+    whole test set, the share of it the gate admits and their worst error, and
+    the throughput of the network, of batched PSTD (64 members per graph) and
+    of the gated pipeline on the test set (batches of 256, device-resident, L2
+    flushed between timed calls).
     """
     import torch
     from paper_2005_00322_gb300.batch import Batch
@@ -433,21 +439,28 @@ def learned_main(args) -> None:
 
     w = inputs.plane128_nn_dd()
     ncells, bc = w.ncells, w.bc
-    ntr, nho = 4096, 128
-    full = inputs.sno_initial_pressures(ntr + nho, seed=1, ncells=ncells)
+    ntr, nte, nho = args.learned_train, 1024, 512
     sl = tuple(slice(stored_node_range(k, b)[0], stored_node_range(k, b)[1] + 1) for k, b in zip(ncells, bc))
-    p0 = torch.tensor(full[(slice(None),) + sl].astype(np.float32), device="cuda")
-    tgt = pstd_reference(ncells, bc, w.dx, w.cfl, w.steps, p0)
+
+    def dataset(n, seed):
+        full = inputs.sno_initial_pressures(n, seed=seed, ncells=ncells)
+        p0 = torch.tensor(full[(slice(None),) + sl].astype(np.float32), device="cuda")
+        return p0, pstd_reference(ncells, bc, w.dx, w.cfl, w.steps, p0)
+    p_tr, t_tr = dataset(ntr, 1)
+    p_te, t_te = dataset(nte, 2)
+    p_ho, t_ho = dataset(nho, 3)
     net = SpectralOperator(ncells, bc, channels=32, modes=16, layers=4, seed=0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    losses = net.train(p0[:ntr], tgt[:ntr], iters=args.learned_iters, batch=16, lr=2e-3)
+    losses = net.train(p_tr, t_tr, iters=args.learned_iters, batch=32, lr=2e-3)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     sur = Surrogate(net, w.dx, w.cfl, w.steps, tol=1e-2)
-    ho_max = sur.validate(p0[ntr:], tgt[ntr:])
-    err = net.rel_err(net.predict(p0[ntr:]), tgt[ntr:]).cpu().numpy()
-    err16 = net.rel_err(net.predict(p0[ntr:], bf16=True), tgt[ntr:]).cpu().numpy()
+    ho_max = sur.validate(p_ho, t_ho)
+    err = net.rel_err(net.predict(p_te), t_te).cpu().numpy()
+    frac = net.high_mode_fraction(p_te).cpu().numpy()
+    admitted = frac < sur.gate
+    err16 = net.rel_err(net.predict(p_te, bf16=True), t_te).cpu().numpy()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
     def timed(fn, samples):
@@ -466,13 +479,14 @@ def learned_main(args) -> None:
             tot += e0.elapsed_time(e1) / 1e3
         return samples * args.steps / tot
 
-    err32 = net.rel_err(net.predict(p0[ntr:], tf32=True), tgt[ntr:]).cpu().numpy()
-    xb = p0[:256].contiguous()
+    xb = p_te[:256].contiguous()
+    # the gated pipeline answers the whole test set; its error against PSTD
+    outs = [sur(p_te[i:i + 256].contiguous()) for i in range(0, nte, 256)]
+    pipe_err = net.rel_err(torch.cat(outs), t_te).cpu().numpy()
     with Clocks(0) as clk:
         net_rate = timed(lambda: net.predict(xb), 256)
         net16_rate = timed(lambda: net.predict(xb, bf16=True), 256)
-        tc_rate = timed(lambda: net.predict(xb, tf32=True), 256)
-    tc_status = net.tensor_core_status()
+        pipe_rate = timed(lambda: sur(xb), 256)
     # PSTD: one batch plan of 64 members, each bench call loads 64 initial
     # pressures, derives u^{-1/2} and runs the 200 steps
     bt = Batch([dict(ncells=ncells, dx=w.dx, bc=bc, cfl=w.cfl)] * 64)
@@ -480,7 +494,7 @@ def learned_main(args) -> None:
 
     def pstd_call():
         for m, (p, us) in enumerate(fields):
-            p.copy_(p0[m])
+            p.copy_(p_te[m])
             for u in us:
                 u.zero_()
         bt.init_velocity(fields)
@@ -488,23 +502,25 @@ def learned_main(args) -> None:
     pstd_rate = timed(pstd_call, 64)
     bt.close()
     line = {
-        "metric": LEARNED_METRIC, "value": net_rate, "unit": "samples/s", "n_gpus": 1, "steps": args.steps,
+        "metric": LEARNED_METRIC, "value": pipe_rate, "unit": "samples/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "plane128_nn_dd_learned", "ncells": list(ncells), "bc": ["".join(b) for b in bc],
                    "cfl": w.cfl, "leapfrog_steps": w.steps, "channels": 32, "modes": 16, "layers": 4,
+                   "inputs": "1-6 blobs, sigma U[2, 8] dx, amplitude U[-1, 1]",
                    "batch": 256, "l2": "flushed (256 MB write) before each timed call"},
         "pstd": {"value": pstd_rate, "unit": "samples/s", "batch": 64},
-        "speedup_vs_pstd": net_rate / pstd_rate,
-        "bf16_weights": {"value": net16_rate, "heldout_max_rel_l2": float(err16.max()),
-                         "heldout_mean_rel_l2": float(err16.mean())},
-        "tf32_tensor_cores": {"value": tc_rate, "speedup_vs_pstd": tc_rate / pstd_rate,
-                              "heldout_max_rel_l2": float(err32.max()),
-                              "heldout_mean_rel_l2": float(err32.mean()), "status": tc_status,
-                              "kernel": "k_tc_gemm (tcgen05.mma kind::tf32, TMEM accumulators)"},
-        "accuracy": {"heldout": nho, "max_rel_l2": float(err.max()), "mean_rel_l2": float(err.mean()),
+        "network": {"value": net_rate, "speedup_vs_pstd": net_rate / pstd_rate},
+        "gated_pipeline": {"value": pipe_rate, "speedup_vs_pstd": pipe_rate / pstd_rate,
+                           "max_rel_l2": float(pipe_err.max()), "share_by_network": float(admitted.mean())},
+        "bf16_weights": {"value": net16_rate, "test_max_rel_l2": float(err16.max()),
+                         "test_median_rel_l2": float(np.median(err16))},
+        "accuracy": {"test": nte, "max_rel_l2": float(err.max()), "median_rel_l2": float(np.median(err)),
+                     "share_within_tol": float((err <= 1e-2).mean()),
+                     "admitted_max_rel_l2": float(err[admitted].max()) if admitted.any() else None,
                      "judge": "PSTD on the same inputs"},
-        "fallback": {"tol": sur.tol, "trusted": sur.trusted, "heldout_max": ho_max},
-        "train": {"samples": ntr, "iters": args.learned_iters, "batch": 16, "seconds": t_train,
+        "gate": {"tol": sur.tol, "high_mode_fraction_below": sur.gate, "heldout": nho,
+                 "heldout_max_rel_l2": ho_max, "heldout_share": sur.routed, "trusted": sur.trusted},
+        "train": {"samples": ntr, "iters": args.learned_iters, "batch": 32, "seconds": t_train,
                   "final_loss": float(np.mean(losses[-50:]))},
         "clocks": clk.summary(),
     }
@@ -528,7 +544,8 @@ def main():
                          "tcgen05; order2: second-order pressure-only form on the FFT passes")
     ap.add_argument("--learned", action="store_true",
                     help="train and time the learned operator against 200 PSTD steps (prints its own line)")
-    ap.add_argument("--learned-iters", type=int, default=8000)
+    ap.add_argument("--learned-iters", type=int, default=12000)
+    ap.add_argument("--learned-train", type=int, default=20000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.learned:

@@ -158,21 +158,23 @@ def plane128_nn_dd(steps: int = 200) -> Workload:
     return Workload("plane128_nn_dd", (128, 128), (("N", "N"), ("D", "D")), 0.3, steps)
 
 
-def sno_initial_pressures(n: int, seed: int, ncells=(128, 128), sigma_cells=(9.0, 12.0),
-                          nblobs=(1, 3), dx=DX) -> np.ndarray:
+def sno_initial_pressures(n: int, seed: int, ncells=(128, 128), sigma_cells=(2.0, 8.0),
+                          nblobs=(1, 6), amp_range=(-1.0, 1.0), dx=DX) -> np.ndarray:
     """n initial pressures on the full node lattice, shape (n, N0+1, N1+1), FP64.
 
-    Each is 1 to 3 Gaussian blobs (count uniform in `nblobs`) of one width
-    sigma ~ U[9, 12] cells and amplitudes ~ U[-1, 1], centres uniform in
-    [4 sigma, L - 4 sigma]: smooth fields whose content beyond the 16th mode
-    of each axis is below 1e-2 of their peak.
+    The learned operator's configured inputs: each sample is 1 to 6 Gaussian
+    blobs (count uniform in `nblobs`), each with its own width sigma ~ U[2, 8]
+    cells and amplitude ~ U[-1, 1], centred uniformly in [4 sigma, L - 4 sigma]
+    per axis.  Generated with numpy's default_rng(seed).
     """
     rng = np.random.default_rng(seed)
     out = np.zeros((n,) + tuple(k + 1 for k in ncells))
     for s in range(n):
         nb = int(rng.integers(nblobs[0], nblobs[1] + 1))
-        sig = float(rng.uniform(*sigma_cells))
-        w = Workload("sample", tuple(ncells), (), 0.3, 0,
-                     random_blobs(ncells, nb, sig, (-1.0, 1.0), int(rng.integers(1 << 30)), dx), dx)
-        out[s] = w.p0_full()
+        blobs = []
+        for _ in range(nb):
+            sig = float(rng.uniform(*sigma_cells)) * dx
+            centre = tuple(float(rng.uniform(4 * sig, k * dx - 4 * sig)) for k in ncells)
+            blobs.append(Blob(centre, sig, float(rng.uniform(*amp_range))))
+        out[s] = Workload("sample", tuple(ncells), (), 0.3, 0, blobs, dx).p0_full()
     return out

@@ -296,8 +296,9 @@ class SpectralOperator:
         return losses.cpu().numpy().tolist()
 
     def predict(self, p0, chunk=256, bf16=False, tf32=None):
-        """Network output for any batch size (processed in chunks); tf32 (default:
-        the operator's setting) runs the GEMMs on the tensor cores."""
+        """Network output for any batch size (processed in chunks).  bf16: the
+        weights rounded to BF16 (the arithmetic stays FP32); tf32 (default: the
+        operator's setting) runs the GEMMs on the tensor cores in TF32."""
         if tf32 is not None and bool(tf32) != self.tf32:
             saved, self.tf32 = self.tf32, bool(tf32)
             try:
@@ -316,6 +317,33 @@ class SpectralOperator:
                 outs.append(self.forward(x, params=prm))
         return outs[0] if len(outs) == 1 else torch.cat(outs)
 
+    def high_mode_fraction(self, p0, chunk=256):
+        """Per-sample ||p - P_K p|| / ||p|| on the device, P_K = Ix Tx (x) Iy Ty
+        the projection onto the first K modes of each axis of the network's
+        basis: the part of an input that no K-mode spectral layer carries.  For
+        the linear wave propagator it is about the smallest error any such
+        network can reach on that input.  Four FP32 GEMMs and a reduction of
+        the library per chunk of samples."""
+        self._check_field(p0, "p0")
+        B, K, X, Y = p0.shape[0], self.K, self.X, self.Y
+        out = self._empty(B)
+        s = self._s()
+
+        def gemm(batch, M, N, Kd, A, sA, Bm, sB, Cm, sC):
+            d = _abi.PstdGemmDesc(batch, M, N, Kd, A.data_ptr(), *sA, Bm.data_ptr(), *sB, Cm.data_ptr(), *sC,
+                                  1.0, 0.0, 1, 0, 0, 0, Kd)
+            self._ck(self.lib.pstd_nn_gemm(ctypes.byref(d), s), "pstd_nn_gemm")
+        for i in range(0, B, chunk):
+            x = p0[i:i + chunk].contiguous()
+            b = x.shape[0]
+            A1, V, A2, low = self._empty(b, X, K), self._empty(b, K, K), self._empty(b, X, K), self._empty(b, X, Y)
+            gemm(1, b * X, K, Y, x, (0, Y, 1), self.Ty, (0, 1, Y), A1, (0, K, 1))
+            gemm(b, K, K, X, self.Tx, (0, X, 1), A1, (X * K, K, 1), V, (K * K, K, 1))
+            gemm(b, X, K, K, self.Ix, (0, K, 1), V, (K * K, K, 1), A2, (X * K, K, 1))
+            gemm(1, b * X, Y, K, A2, (0, K, 1), self.Iy, (0, 1, K), low, (0, Y, 1))
+            out[i:i + b].copy_(self.rel_err(low, x))
+        return out
+
     def rel_err(self, a, ref):
         """Per-sample ||a - ref|| / ||ref|| on the device (FP64 sums)."""
         err = self._empty(a.shape[0])
@@ -324,75 +352,143 @@ class SpectralOperator:
         return err
 
 
+class PstdRunner:
+    """The solver's answers for batches of initial pressures: one batch plan
+    of `group` independent members (pstd_batch_*), kept and reused; requests
+    run `group` at a time (a short last group is padded with zero fields)."""
+
+    def __init__(self, ncells, bc, dx, cfl, steps, c0=1500.0, rho0=1000.0, group=64, device=None):
+        from .batch import Batch
+        self.steps, self.group = int(steps), int(group)
+        self.batch = Batch([dict(ncells=ncells, dx=dx, bc=bc, cfl=cfl, c0=c0, rho0=rho0)] * self.group,
+                           device=device)
+        self.fields = self.batch.zeros()
+
+    def __call__(self, p0s):
+        out = torch.empty_like(p0s)
+        B, n = p0s.shape[0], self.group
+        for g0 in range(0, B, n):
+            k = min(n, B - g0)
+            for m, (p, us) in enumerate(self.fields):
+                if m < k:
+                    p.copy_(p0s[g0 + m])
+                else:
+                    p.zero_()
+                for u in us:
+                    u.zero_()
+            self.batch.init_velocity(self.fields)
+            self.batch.run(self.fields, self.steps)
+            for m in range(k):
+                out[g0 + m].copy_(self.fields[m][0])
+        return out
+
+    def close(self):
+        self.batch.close()
+
+
 def pstd_reference(ncells, bc, dx, cfl, steps, p0s, c0=1500.0, rho0=1000.0, group=64):
     """The solver's answer for every sample of p0s (B, X, Y): `steps` leapfrog
-    steps from zero velocity (half-step rule), run `group` samples at a time as
-    one batch of independent members."""
-    from .batch import Batch
-    out = torch.empty_like(p0s)
-    B = p0s.shape[0]
-    for g0 in range(0, B, group):
-        n = min(group, B - g0)
-        bt = Batch([dict(ncells=ncells, dx=dx, bc=bc, cfl=cfl, c0=c0, rho0=rho0)] * n, device=p0s.device)
-        fields = bt.zeros()
-        for m, (p, us) in enumerate(fields):
-            p.copy_(p0s[g0 + m])
-        bt.init_velocity(fields)
-        bt.run(fields, steps)
-        for m, (p, _) in enumerate(fields):
-            out[g0 + m].copy_(p)
-        bt.close()
-    return out
+    steps from zero velocity (half-step rule), `group` samples at a time as one
+    batch of independent members."""
+    if p0s.shape[0] == 0:
+        return torch.empty_like(p0s)
+    r = PstdRunner(ncells, bc, dx, cfl, steps, c0, rho0, min(group, p0s.shape[0]), p0s.device)
+    try:
+        return r(p0s)
+    finally:
+        r.close()
 
 
 class Surrogate:
     """The learned operator with the solver as judge.
 
-    ``validate`` compares the network with PSTD on a held-out set and trusts it
-    only if the worst per-sample relative error is within ``tol``.  A call
-    answers with PSTD when the network is not trusted; otherwise with the
-    network, and every ``audit_every``-th call also runs PSTD on one sampled
-    request and falls back (answering that call with PSTD and distrusting the
-    network) if its error exceeds ``tol``.
+    ``validate`` compares the network with PSTD on a held-out set.  A K-mode
+    spectral network cannot carry the part of an input above its K-th mode, so
+    each request is gated by that part's share, ``high_mode_fraction`` r: the
+    network answers only requests with r below the gate, and PSTD all others.
+    The gate is set on the held-out set: walking its samples by increasing r,
+    the first whose error exceeds ``safety`` x ``tol`` fixes it at ``margin``
+    times that sample's r (no gate if none does), so that the admitted held-out
+    samples keep a margin below ``tol``.  The network is trusted while some held-out sample lies below the
+    gate.  Every ``audit_every``-th call also runs PSTD on one network-answered
+    request and, if its error exceeds ``tol``, answers the call with PSTD and
+    stops trusting the network.
     """
 
     def __init__(self, net: SpectralOperator, dx, cfl, steps, tol=1e-2, audit_every=16, seed=0,
-                 c0=1500.0, rho0=1000.0):
+                 c0=1500.0, rho0=1000.0, margin=0.9, safety=0.7):
         self.net, self.dx, self.cfl, self.steps, self.tol = net, dx, cfl, int(steps), float(tol)
-        self.c0, self.rho0 = c0, rho0
+        self.c0, self.rho0, self.margin, self.safety = c0, rho0, float(margin), float(safety)
+        self._runner = None
         self.audit_every = int(audit_every)
         self.trusted = False
+        self.gate = 0.0
+        self.routed = 0.0
         self.calls = 0
         self.last_source = None
+        self.last_routed = 0
         self.heldout_err = None
         self.audits = []
         self._rng = np.random.default_rng(seed)
 
     def _pstd(self, p0s):
-        return pstd_reference(self.net.ncells, self.net.bc, self.dx, self.cfl, self.steps, p0s, self.c0, self.rho0)
+        if self._runner is None:
+            self._runner = PstdRunner(self.net.ncells, self.net.bc, self.dx, self.cfl, self.steps, self.c0,
+                                      self.rho0, device=p0s.device)
+        return self._runner(p0s)
+
+    def close(self):
+        if self._runner is not None:
+            self._runner.close()
+            self._runner = None
 
     def validate(self, p0s, targets=None):
+        """Held-out check: returns the network's worst relative error on p0s and
+        sets the gate and the share of held-out samples it admits."""
         if targets is None:
             targets = self._pstd(p0s)
-        err = self.net.rel_err(self.net.predict(p0s), targets)
+        err = self.net.rel_err(self.net.predict(p0s), targets).cpu().numpy()
+        frac = self.net.high_mode_fraction(p0s).cpu().numpy()
         self.heldout_err = float(err.max())
-        self.trusted = self.heldout_err <= self.tol
+        bad = frac[err > self.safety * self.tol]
+        self.gate = self.margin * float(bad.min()) if bad.size else math.inf
+        self.routed = float((frac < self.gate).mean())
+        self.trusted = self.routed > 0
         return self.heldout_err
 
     def __call__(self, p0s):
         self.calls += 1
         if not self.trusted:
+            self.last_source, self.last_routed = "pstd", 0
+            return self._pstd(p0s)
+        if math.isinf(self.gate):
+            mask = torch.ones(p0s.shape[0], dtype=torch.bool, device=p0s.device)
+        else:
+            mask = self.net.high_mode_fraction(p0s) < self.gate
+        net_idx = torch.nonzero(mask).flatten()
+        n_net = int(net_idx.numel())
+        self.last_routed = n_net
+        if n_net == 0:
             self.last_source = "pstd"
             return self._pstd(p0s)
-        out = self.net.predict(p0s)
+        if n_net == p0s.shape[0]:
+            out = self.net.predict(p0s)
+            net_out, sel = out, net_idx
+        else:
+            out = torch.empty_like(p0s)
+            sel = net_idx
+            net_out = self.net.predict(p0s.index_select(0, sel).contiguous())
+            out.index_copy_(0, sel, net_out)
+            rest = torch.nonzero(~mask).flatten()
+            out.index_copy_(0, rest, self._pstd(p0s.index_select(0, rest).contiguous()))
         if self.audit_every > 0 and self.calls % self.audit_every == 0:
-            i = int(self._rng.integers(p0s.shape[0]))
-            ref = self._pstd(p0s[i:i + 1].contiguous())
-            e = float(self.net.rel_err(out[i:i + 1].contiguous(), ref)[0])
+            i = int(self._rng.integers(n_net))
+            ref = self._pstd(p0s[int(sel[i])].unsqueeze(0).contiguous())
+            e = float(self.net.rel_err(net_out[i:i + 1].contiguous(), ref)[0])
             self.audits.append(e)
             if e > self.tol:
                 self.trusted = False
-                self.last_source = "pstd"
+                self.last_source, self.last_routed = "pstd", 0
                 return self._pstd(p0s)
-        self.last_source = "network"
+        self.last_source = "network" if n_net == p0s.shape[0] else "mixed"
         return out

@@ -355,3 +355,72 @@ def test_training_reduces_loss_and_fallback():
     out = sur(p0[80:88].contiguous())
     assert sur.last_source == "pstd" and not sur.trusted and len(sur.audits) == 2
     assert torch.equal(out, tgt[80:88])
+
+
+def test_learned_operator_on_configured_inputs():
+    """The configured workload: 128^2 NN / DD box, 200 steps, inputs of 1-6
+    blobs with sigma U[2, 8] dx; trained on 20k PSTD answers (seed 1), gated on
+    512 held-out samples (seed 3), judged on the 1k test set (seed 2).
+
+    A 16-mode network cannot carry an input's content above the 16th mode, so
+    on this distribution it is within 1e-2 of PSTD only for its smooth end.
+    Asserted: the gated pipeline answers every test sample within 1e-2 of PSTD
+    (the network where the gate admits the input, PSTD bit for bit elsewhere);
+    on the smooth end of the distribution (single blobs of sigma 7.5-8 dx) the
+    gate admits at least a quarter of the inputs, every answer is within 1e-2,
+    and the network gives at least 3x the predictions/s of 200 batched PSTD
+    steps."""
+    from paper_2005_00322_gb300.sno import PstdRunner, SpectralOperator, Surrogate
+    from paper_2005_00322_gb300.solver import stored_node_range
+    w = inputs.plane128_nn_dd()
+    ncells, bc = w.ncells, w.bc
+    sl = tuple(slice(stored_node_range(k, b)[0], stored_node_range(k, b)[1] + 1) for k, b in zip(ncells, bc))
+    runner = PstdRunner(ncells, bc, w.dx, w.cfl, w.steps)
+
+    def dataset(n, seed, **kw):
+        p0 = _dev(inputs.sno_initial_pressures(n, seed, ncells=ncells, **kw)[(slice(None),) + sl])
+        return p0, runner(p0)
+    p_tr, t_tr = dataset(20000, 1)
+    p_te, t_te = dataset(1024, 2)
+    p_ho, t_ho = dataset(512, 3)
+    net = SpectralOperator(ncells, bc, channels=32, modes=16, layers=4, seed=0)
+    net.train(p_tr, t_tr, iters=12000, batch=32, lr=2e-3)
+    sur = Surrogate(net, w.dx, w.cfl, w.steps, tol=1e-2)
+    sur.validate(p_ho, t_ho)
+
+    # the whole configured test set: every answer within the tolerance
+    out = torch.cat([sur(p_te[i:i + 256].contiguous()) for i in range(0, 1024, 256)])
+    assert net.rel_err(out, t_te).max().item() <= 1e-2
+    admitted = (net.high_mode_fraction(p_te) < sur.gate).cpu().numpy()
+    rest = np.nonzero(~admitted)[0]
+    assert torch.equal(out[rest], t_te[rest])
+    net_err = net.rel_err(net.predict(p_te), t_te).cpu().numpy()
+    print(f"configured test set: network within 1e-2 for {(net_err <= 1e-2).mean():.3f}, median error "
+          f"{np.median(net_err):.3g}; gate {sur.gate:.3g} admits {admitted.mean():.3f}")
+
+    # the smooth end of the configured distribution (single blobs of sigma
+    # 7.5-8 dx, whose share above the 16th mode straddles the gate): the
+    # network answers a good part of it, every answer within the tolerance
+    p_sm, t_sm = dataset(256, 4, sigma_cells=(7.5, 8.0), nblobs=(1, 1))
+    out = sur(p_sm)
+    assert sur.last_source in ("network", "mixed") and sur.last_routed >= 64
+    assert net.rel_err(out, t_sm).max().item() <= 1e-2
+
+    # measured gain on the requests the network answers: predictions/s of the
+    # network against the same 200 steps run as batched PSTD (64 members)
+    def rate(fn, n, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return n * reps / (e0.elapsed_time(e1) / 1e3)
+    net_rate = rate(lambda: net.predict(p_sm), 256)
+    pstd_rate = rate(lambda: runner(p_sm), 256)
+    print(f"network {net_rate:.0f}/s, PSTD {pstd_rate:.0f}/s")
+    assert net_rate >= 3.0 * pstd_rate
+    sur.close()
+    runner.close()
