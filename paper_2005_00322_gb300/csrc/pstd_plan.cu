@@ -127,6 +127,10 @@ struct Axis {
     uint16_t* d_tc16[2] = {nullptr, nullptr};
     CUtensorMap tc16_map[2];
     int tc16_MT[2] = {0, 0}, tc16_KC[2] = {0, 0};
+    // the padded fields along this axis: X maps of p and u_a, Y (and Cin)
+    // maps of u_a, p and the accumulator; line tiles
+    CUtensorMap tc16_x[2], tc16_y[3];
+    int64_t tc16_tiles = 0, tc16_tpo = 0;
     // split-precision dense form
     uint4* d_gemm = nullptr;          // A1h | A1l | A2h | A2l fragments
     pstd::GemmAxis gax{};
@@ -226,6 +230,11 @@ struct pstd_plan_s {
     Axis ax[3];
     float* d_S = nullptr;
     double* d_energy = nullptr;       // pstd_energy's FP64 partial sums, on first use
+    // BF16 split form: plan-owned copies of p, u_0.. and the accumulator with
+    // the last dimension padded to a multiple of 4 floats (TMA strides)
+    float* d_pad[4] = {};
+    float* d_Spad = nullptr;
+    int64_t pitch[4] = {};
     int64_t last_launches = 0;
     GraphEntry graphs[kGraphCache];
     uint64_t stamp = 0;
@@ -1002,9 +1011,78 @@ void free_plan_memory(pstd_plan_s* P) {
     }
     cudaFree(P->d_S);
     cudaFree(P->d_energy);
+    for (auto* b : P->d_pad) cudaFree(b);
+    cudaFree(P->d_Spad);
     cudaFree(P->d_sync);
     for (auto& g : P->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
+}
+
+// BF16 split form: the padded copies of p, u_0.. and the accumulator (last
+// dimension rounded up to 4 floats, zero-filled) and every axis's tensor maps.
+int tc16_setup(pstd_plan_s* P) {
+    const int d = P->ndim;
+    auto rows_of = [&](int f) {
+        int64_t r = 1;
+        for (int j = 0; j < d - 1; ++j) r *= P->shape[f][j];
+        return r;
+    };
+    for (int f = 0; f <= d; ++f) {
+        P->pitch[f] = (P->shape[f][d - 1] + 3) / 4 * 4;
+        const size_t bytes = (size_t)rows_of(f) * P->pitch[f] * sizeof(float);
+        cudaError_t e = cudaMalloc((void**)&P->d_pad[f], bytes);
+        if (e == cudaSuccess) e = cudaMemset(P->d_pad[f], 0, bytes);
+        if (e == cudaSuccess && f == 0) e = cudaMalloc((void**)&P->d_Spad, bytes);
+        if (e == cudaSuccess && f == 0) e = cudaMemset(P->d_Spad, 0, bytes);
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? PSTD_ENOMEM : cuda_fail(e, "cudaMalloc(padded)");
+    }
+    for (int a = 0; a < d; ++a) {
+        Axis& A = P->ax[a];
+        const int contig = a == d - 1;
+        // fields along this axis: 0 = p (and S), a + 1 = u_a
+        auto map = [&](int f, float* base, int ymap, CUtensorMap* m) {
+            const int64_t len = P->shape[f][a];
+            if (contig) return pstd::tc16_field_map(base, 1, len, rows_of(f), 1, P->pitch[f], ymap, m);
+            int64_t inner = P->pitch[f], outer = 1;
+            for (int j = a + 1; j < d - 1; ++j) inner *= P->shape[f][j];
+            for (int j = 0; j < a; ++j) outer *= P->shape[f][j];
+            return pstd::tc16_field_map(base, 0, len, inner, outer, P->pitch[f], ymap, m);
+        };
+        int r = map(0, P->d_pad[0], 0, &A.tc16_x[0]);
+        if (r == 0) r = map(a + 1, P->d_pad[a + 1], 0, &A.tc16_x[1]);
+        if (r == 0) r = map(a + 1, P->d_pad[a + 1], 1, &A.tc16_y[0]);
+        if (r == 0) r = map(0, P->d_pad[0], 1, &A.tc16_y[1]);
+        if (r == 0) r = map(0, P->d_Spad, 1, &A.tc16_y[2]);
+        if (r != 0) return cuda_fail(cudaErrorNotSupported, "cuTensorMapEncodeTiled(field)");
+        if (contig) {
+            A.tc16_tpo = 0;
+            A.tc16_tiles = (rows_of(0) + 127) / 128;
+        } else {
+            int64_t inner = P->pitch[0], outer = 1;
+            for (int j = a + 1; j < d - 1; ++j) inner *= P->shape[0][j];
+            for (int j = 0; j < a; ++j) outer *= P->shape[0][j];
+            A.tc16_tpo = (inner + 127) / 128;
+            A.tc16_tiles = outer * A.tc16_tpo;
+        }
+    }
+    return PSTD_OK;
+}
+
+// Copy the caller's fields into the padded copies (in = true) or back.
+int tc16_copy(pstd_plan_s* P, float* p, float* const* u, bool in) {
+    const int d = P->ndim;
+    for (int f = 0; f <= d; ++f) {
+        float* user = f == 0 ? p : u[f - 1];
+        int64_t rows = 1;
+        for (int j = 0; j < d - 1; ++j) rows *= P->shape[f][j];
+        const size_t w = (size_t)P->shape[f][d - 1] * sizeof(float), pw = (size_t)P->pitch[f] * sizeof(float);
+        cudaError_t e = in ? cudaMemcpy2DAsync(P->d_pad[f], pw, user, w, w, (size_t)rows, cudaMemcpyDeviceToDevice,
+                                               P->stream)
+                           : cudaMemcpy2DAsync(user, w, P->d_pad[f], pw, w, (size_t)rows, cudaMemcpyDeviceToDevice,
+                                               P->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2DAsync(padded field)");
+    }
+    return PSTD_OK;
 }
 
 int validate(const pstd_desc* d) {
@@ -1123,21 +1201,18 @@ int launch_step(pstd_plan_s* P, float* p, float* const* u, int64_t* launches) {
             continue;
         }
         if (P->opts.form == 3) {
-            // u_a += D1 p, then acc_out = acc_in + D2 u_a, over the lines of the axis
+            // on the plan's padded fields: u_a += D1 p, then acc_out = acc_in + D2 u_a
             int* status = (int*)(P->d_sync + 2);
+            const int contig = a == P->ndim - 1;
             pstd::Tc16Gemm g1{};
             g1.K = A.lp; g1.Mout = A.nu; g1.MT = A.tc16_MT[0]; g1.KC = A.tc16_KC[0];
-            g1.nlines = A.nlines; g1.inner = A.inner;
-            g1.X = p; g1.Cin = u[a]; g1.Y = u[a]; g1.status = status;
-            CK(pstd::tc16_launch(A.tc16_map[0], g1, P->stream));
-            pstd::Tc16Gemm g2{};
+            g1.contiguous = contig; g1.tiles = A.tc16_tiles; g1.tpo = A.tc16_tpo; g1.status = status;
+            CK(pstd::tc16_launch(A.tc16_map[0], A.tc16_x[0], A.tc16_y[0], A.tc16_y[0], g1, P->stream));
+            pstd::Tc16Gemm g2 = g1;
             g2.K = A.nu; g2.Mout = A.lp; g2.MT = A.tc16_MT[1]; g2.KC = A.tc16_KC[1];
-            g2.nlines = A.nlines; g2.inner = A.inner;
-            g2.X = u[a];
-            g2.Cin = (a == P->ndim - 1) ? p : P->d_S;
-            g2.Y = (a == 0) ? p : P->d_S;
-            g2.status = status;
-            CK(pstd::tc16_launch(A.tc16_map[1], g2, P->stream));
+            const CUtensorMap& cin = (a == P->ndim - 1) ? A.tc16_y[1] : A.tc16_y[2];
+            const CUtensorMap& out = (a == 0) ? A.tc16_y[1] : A.tc16_y[2];
+            CK(pstd::tc16_launch(A.tc16_map[1], A.tc16_x[1], cin, out, g2, P->stream));
             *launches += 2;
             continue;
         }
@@ -1322,6 +1397,7 @@ int pstd_internal_convert_velocity(pstd_plan_t* P, float* const* u, int to_spect
 }
 
 int pstd_internal_launch_steps(pstd_plan_t* P, float* p, float* const* u, int64_t n, int64_t* launches) {
+    if (P->opts.form == 3) return PSTD_EUNSUPPORTED;     // steps on the plan's padded copies only
     for (int64_t s = 0; s < n; ++s) {
         int rc = launch_step(P, p, u, launches);
         if (rc != PSTD_OK) return rc;
@@ -1418,6 +1494,7 @@ int pstd_plan_ex(const pstd_desc* desc, void* stream, const pstd_plan_opts* opts
         P->shape[f][f - 1] = desc->ncells[f - 1] - (desc->bc[f - 1][1] == PSTD_NEUMANN_MID ? 1 : 0);
     }
     for (int i = 0; i < P->ndim && rc == PSTD_OK; ++i) rc = build_axis(P, i);
+    if (rc == PSTD_OK && P->opts.form == 3) rc = tc16_setup(P);
     if (rc == PSTD_OK && (P->opts.form == 2 || P->opts.form == 3)) {
         // status word of the tensor-core GEMMs' bounded waits (read by pstd_sync)
         cudaError_t e = cudaMalloc((void**)&P->d_sync, 4 * sizeof(unsigned));
@@ -1563,6 +1640,13 @@ int pstd_step(pstd_plan_t* P, float* p, float* const* u) {
     for (int a = 0; a < P->ndim; ++a)
         if (!u[a]) return PSTD_EINVAL;
     P->last_launches = 0;
+    if (P->opts.form == 3) {
+        // the step runs on the plan's padded copies
+        int rc = tc16_copy(P, p, u, true);
+        if (rc == PSTD_OK) rc = launch_step(P, P->d_pad[0], P->d_pad + 1, &P->last_launches);
+        if (rc == PSTD_OK) rc = tc16_copy(P, p, u, false);
+        return rc;
+    }
     int rc = convert_velocity(P, u, 2, &P->last_launches);
     if (rc == PSTD_OK) rc = launch_step(P, p, u, &P->last_launches);
     if (rc == PSTD_OK) rc = convert_velocity(P, u, 3, &P->last_launches);
@@ -1579,6 +1663,13 @@ int pstd_run(pstd_plan_t* P, float* p, float* const* u, int64_t nsteps) {
         if (!u[a]) return PSTD_EINVAL;
     P->last_launches = 0;
     if (nsteps == 0) return PSTD_OK;
+    if (P->opts.form == 3) {
+        // the steps run on the plan's padded copies (one graph for every call)
+        int rc = tc16_copy(P, p, u, true);
+        if (rc == PSTD_OK) rc = run_steps(P, P->d_pad[0], P->d_pad + 1, nsteps);
+        if (rc == PSTD_OK) rc = tc16_copy(P, p, u, false);
+        return rc;
+    }
     int64_t conv = 0;
     int rc = convert_velocity(P, u, 2, &conv);
     if (rc == PSTD_OK) rc = run_steps(P, p, u, nsteps);

@@ -28,6 +28,12 @@
 // the whole k range (their truncation is 2^-8 smaller); Dm Xl, Dl Xm and
 // Dl Xl (2^-23 and below) are dropped.  Y = Cin + (S + X).
 //
+// Fields are read and written by TMA: the plan keeps p, the velocities and
+// the accumulator in its own copies whose last dimension is padded to a
+// multiple of 4 floats, so that every tensor map stride is a multiple of 16
+// bytes.  Lines and rows beyond a field's extent read as zeros and are not
+// written (the tensor maps carry the true extents).
+//
 // Persistent kernel, one CTA per SM, walking (line tile, output tile) pairs:
 // a tile is 128 output rows (MMA M) x 128 lines (MMA N); the MMAs run on
 // 16-wide k chunks.
@@ -36,13 +42,14 @@
 //   warp 1      allocates tensor memory; one thread issues the 6 MMAs of each
 //               chunk and commits them to the stage's mbarrier and, at the
 //               end of a block, to the block's accumulator mbarrier;
-//   warps 2-5   converters: copy the field's 32-wide blocks into a 4-deep
-//               ring in shared memory (cp.async, three blocks in flight), then
-//               per block find each line's maximum, split and store the three
-//               slices in the MMA's K-major 32-byte-swizzled layout;
-//   warps 6-9   epilogue: add each block's L0 into S; at the end of a tile move
-//               S + X into a shared output tile (which frees tensor memory for
-//               the next tile) and write Y = Cin + S + X with coalesced accesses.
+//   warps 2-5   converters: the field's 32-wide blocks arrive by TMA in a
+//               4-deep ring (three in flight); per block each thread finds its
+//               line's maximum, splits the values and stores the three slices
+//               in the MMA's K-major 32-byte-swizzled layout;
+//   warps 6-9   epilogue: the tile's Cin arrives by TMA in a shared output
+//               tile while the blocks run; each block's L0 is added into S;
+//               at the end S + X is added into the output tile (which frees
+//               tensor memory for the next tile) and a TMA store writes Y.
 // Every wait is bounded: a wait that gives up sets *status and a shared abort
 // flag that ends every other wait, the MMAs and copies in flight are waited
 // for (bounded), and tensor memory is freed.
@@ -62,13 +69,11 @@ constexpr int NL = 128;                        // lines per tile (MMA N)
 constexpr int BK = 16;                         // k per MMA chunk: one 32-byte swizzle row of BF16
 constexpr int KB = 32;                         // k per scale block (two chunks)
 constexpr int STAGES = 3;
-constexpr int RING = 4;                        // raw field blocks in shared memory
+constexpr int RING = 4;                        // field blocks in shared memory (three in flight)
 constexpr uint32_t PLANE = BM * BK * 2;        // one BF16 slice of one chunk: 4 KB
 constexpr uint32_t STAGE_BYTES = 6 * PLANE;    // operator Dh Dm Dl, field Xh Xm Xl
-constexpr int RAW_LD = KB + 1;                 // contiguous layout: [line][k], padded
-constexpr uint32_t RAW_BYTES = NL * RAW_LD * 4;
-constexpr int OB_LD = NL + 1;                  // output tile row (padded)
-constexpr uint32_t OB_BYTES = BM * OB_LD * 4;
+constexpr uint32_t RAW_BYTES = NL * KB * 4;    // one FP32 field block: 16 KB
+constexpr uint32_t OB_BYTES = BM * NL * 4;     // the output tile: 64 KB
 constexpr size_t SMEM = STAGES * STAGE_BYTES + RING * RAW_BYTES + OB_BYTES + 1024;
 constexpr int THREADS = 320;
 constexpr uint32_t TMEM_COLS = 512;            // L0[0] 0, L0[1] 128, X 256, S 384
@@ -137,13 +142,34 @@ __device__ __forceinline__ bool group_and(int id, bool v) {
 }
 __device__ __forceinline__ void group_sync(int id) { asm volatile("bar.sync %0, 128;\n" ::"r"(id) : "memory"); }
 
-// 4-byte asynchronous copy global -> shared; `n` = 0 stores a zero.
-__device__ __forceinline__ void cp4(uint32_t dst, const float* src, int n) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(n) : "memory");
+// TMA tile loads into this CTA's shared memory, completing on an mbarrier.
+__device__ __forceinline__ void tma_load2(uint32_t dst, const CUtensorMap* m, uint32_t bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];\n" ::"r"(
+            dst),
+        "l"((uint64_t)m), "r"(bar), "r"(c0), "r"(c1)
+        : "memory");
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* m, uint32_t bar, int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+        "[%2];\n" ::"r"(dst),
+        "l"((uint64_t)m), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+// TMA tile stores from shared memory (bulk async group of this thread).
+__device__ __forceinline__ void tma_store2(const CUtensorMap* m, uint32_t src, int c0, int c1) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%2, %3}], [%1];\n" ::"l"(
+                     (uint64_t)m),
+                 "r"(src), "r"(c0), "r"(c1)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_store3(const CUtensorMap* m, uint32_t src, int c0, int c1, int c2) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4}], [%1];\n" ::"l"(
+                     (uint64_t)m),
+                 "r"(src), "r"(c0), "r"(c1), "r"(c2)
+                 : "memory");
+}
 
 // K-major operand tile with 32-byte swizzle: rows of 32 bytes, 8-row groups
 // 256 bytes apart (SBO); the leading offset is unused for this layout.
@@ -221,29 +247,50 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 }
 #endif
 
-__global__ void __launch_bounds__(THREADS, 1) k_tc16(const __grid_constant__ CUtensorMap map, const Tc16Gemm g) {
+__global__ void __launch_bounds__(THREADS, 1)
+    k_tc16(const __grid_constant__ CUtensorMap mop, const __grid_constant__ CUtensorMap mx,
+           const __grid_constant__ CUtensorMap mcin, const __grid_constant__ CUtensorMap my, const Tc16Gemm g) {
 #ifdef __CUDA_ARCH__
     extern __shared__ uint8_t tc16_raw[];
-    __shared__ __align__(8) uint64_t bars[3 * STAGES + 6];
+    __shared__ __align__(8) uint64_t bars[3 * STAGES + RING + 7];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     uint8_t* sm = (uint8_t*)(((uintptr_t)tc16_raw + 1023) & ~(uintptr_t)1023);
-    float* RAW = reinterpret_cast<float*>(sm + STAGES * STAGE_BYTES);
+    uint8_t* RAW = sm + STAGES * STAGE_BYTES;
     float* OB = reinterpret_cast<float*>(sm + STAGES * STAGE_BYTES + RING * RAW_BYTES);
     const uint32_t sbase = smem_u32(sm);
+    const uint32_t rbase = sbase + STAGES * STAGE_BYTES, obase = rbase + RING * RAW_BYTES;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nc = g.KC;                        // 16-wide chunks per tile
     const int nb = (nc + 1) / 2;                // 32-wide blocks per tile
-    const int64_t ntiles = ((g.nlines + NL - 1) / NL) * g.MT;
+    const int64_t ntiles = g.tiles * g.MT;
     volatile int* abortp = &abort_flag;
     auto bar = [&](int i) { return smem_u32(&bars[i]); };
-    // tma_full[S], cvt_full[S], empty[S], blk_full[2], blk_empty[2], acc_empty, final
-    const int TMA_FULL = 0, CVT_FULL = STAGES, EMPTY = 2 * STAGES, BLK_FULL = 3 * STAGES,
-              BLK_EMPTY = BLK_FULL + 2, ACC_EMPTY = BLK_FULL + 4, FINAL = BLK_FULL + 5;
-    auto tile_of = [&](int64_t j, int& mt, int64_t& l0) {
+    // tma_full[S], cvt_full[S], empty[S], raw_full[RING], blk_full[2],
+    // blk_empty[2], acc_empty, cin_full, final
+    const int TMA_FULL = 0, CVT_FULL = STAGES, EMPTY = 2 * STAGES, RAW_FULL = 3 * STAGES,
+              BLK_FULL = RAW_FULL + RING, BLK_EMPTY = BLK_FULL + 2, ACC_EMPTY = BLK_FULL + 4,
+              CIN_FULL = BLK_FULL + 5, FINAL = BLK_FULL + 6;
+    // the j-th tile of this CTA: output tile mt, line tile lt -> TMA
+    // coordinates of its lines (contiguous axis: row l0; strided: inner i0 of
+    // outer block o)
+    struct TileAt {
+        int mt, l0, i0, o;
+    };
+    auto tile_of = [&](int64_t j) {
         const int64_t tix = (int64_t)blockIdx.x + j * gridDim.x;
-        mt = (int)(tix % g.MT);
-        l0 = (tix / g.MT) * NL;
+        TileAt t;
+        t.mt = (int)(tix % g.MT);
+        const int64_t lt = tix / g.MT;
+        if (g.contiguous) {
+            t.l0 = (int)(lt * NL);
+            t.i0 = t.o = 0;
+        } else {
+            t.o = (int)(lt / g.tpo);
+            t.i0 = (int)((lt % g.tpo) * NL);
+            t.l0 = 0;
+        }
+        return t;
     };
     const int64_t my_tiles = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
@@ -254,14 +301,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc16(const __grid_constant__ CUt
             mbar_init(bar(CVT_FULL + s), 4);
             mbar_init(bar(EMPTY + s), 1);
         }
+        for (int r = 0; r < RING; ++r) mbar_init(bar(RAW_FULL + r), 1);
         for (int b = 0; b < 2; ++b) {
             mbar_init(bar(BLK_FULL + b), 1);
             mbar_init(bar(BLK_EMPTY + b), 4);
         }
         mbar_init(bar(ACC_EMPTY), 4);
+        mbar_init(bar(CIN_FULL), 1);
         mbar_init(bar(FINAL), 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];\n" ::"l"((uint64_t)&map) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"((uint64_t)&mop) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"((uint64_t)&mx) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"((uint64_t)&mcin) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"((uint64_t)&my) : "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
@@ -282,9 +334,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc16(const __grid_constant__ CUt
             int64_t gc = 0;                 // chunk count over this CTA's tiles
             bool ok = true;
             for (int64_t j = 0; j < my_tiles && ok; ++j) {
-                int mt;
-                int64_t l0;
-                tile_of(j, mt, l0);
+                const TileAt t = tile_of(j);
                 for (int c = 0; c < nc; ++c, ++gc) {
                     const int s = (int)(gc % STAGES);
                     const int64_t n = gc / STAGES;
@@ -293,11 +343,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc16(const __grid_constant__ CUt
                         break;
                     }
                     mbar_expect_tx(bar(TMA_FULL + s), 3 * PLANE);
-                    asm volatile(
-                        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                        " [%0], [%1, {%3, %4, %5}], [%2];\n" ::"r"(sbase + (uint32_t)s * STAGE_BYTES),
-                        "l"((uint64_t)&map), "r"(bar(TMA_FULL + s)), "r"(c * BK), "r"(mt * BM), "r"(0)
-                        : "memory");
+                    tma_load3(sbase + (uint32_t)s * STAGE_BYTES, &mop, bar(TMA_FULL + s), c * BK, t.mt * BM, 0);
                     issued[s] = (int)(n + 1);
                 }
             }
@@ -349,89 +395,70 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc16(const __grid_constant__ CUt
             drain_bar(bar(FINAL), 0u, g.status);
         }
     } else if (warp < 6) {
-        // ---- converters (128 threads): thread t owns line l0 + t of each tile ----
-        const int cw = warp - 2, t = tid - 64;
-        // copies of block p of tile j into ring slot (total block count) % RING
-        auto issue_block = [&](int64_t j, int p, int slot) {
-            int mt;
-            int64_t l0;
-            tile_of(j, mt, l0);
-            float* raw = RAW + (size_t)slot * (RAW_BYTES / 4);
-            const int k0 = p * KB;
-            if (g.inner > 1) {
-                // raw[k][line]: thread t copies its own line
-                const int64_t l = l0 + t;
-                const bool valid = l < g.nlines;
-                const float* xp = g.X + (valid ? (l / g.inner) * (int64_t)g.K * g.inner + (l % g.inner) : 0);
-#pragma unroll 8
-                for (int k = 0; k < KB; ++k) {
-                    const bool in = valid && k0 + k < g.K;
-                    cp4(smem_u32(raw + k * NL + t), in ? xp + (int64_t)(k0 + k) * g.inner : g.X, in ? 4 : 0);
-                }
-            } else {
-                // raw[line][k] (padded rows): warp cw copies its 32 lines, lane = k
-#pragma unroll 8
-                for (int jj = 0; jj < 32; ++jj) {
-                    const int r = 32 * cw + jj;
-                    const int64_t l = l0 + r;
-                    const bool in = l < g.nlines && k0 + lane < g.K;
-                    cp4(smem_u32(raw + r * RAW_LD + lane), in ? g.X + l * (int64_t)g.K + k0 + lane : g.X, in ? 4 : 0);
-                }
-            }
-        };
+        // ---- converters (128 threads): thread t owns line t of each tile ----
+        const int t = tid - 64;
         // the blocks in order over this CTA's tiles: (tile, block) of index q
         int64_t qj = 0;
         int qp = 0;
-        auto next_q = [&]() {
+        auto issue_next = [&](int slot) {       // thread 0: the next block into `slot`
+            if (qj >= my_tiles) return false;
+            const TileAt tl = tile_of(qj);
+            const uint32_t dst = rbase + (uint32_t)slot * RAW_BYTES;
+            mbar_expect_tx(bar(RAW_FULL + slot), RAW_BYTES);
+            if (g.contiguous) tma_load2(dst, &mx, bar(RAW_FULL + slot), qp * KB, tl.l0);
+            else tma_load3(dst, &mx, bar(RAW_FULL + slot), tl.i0, qp * KB, tl.o);
             if (++qp == nb) {
                 qp = 0;
                 ++qj;
             }
+            return true;
         };
-        // fill the ring: RING - 1 blocks ahead
-        int64_t issued = 0;
-        for (int i = 0; i < RING - 1; ++i) {
-            if (qj < my_tiles) {
-                issue_block(qj, qp, (int)(issued % RING));
-                next_q();
-            }
-            cp_commit();
-            ++issued;
-        }
-        int64_t gc = 0, done = 0;
-        bool ok = true;
-        for (int64_t j = 0; j < my_tiles && ok; ++j) {
-            for (int p = 0; p < nb && ok; ++p, ++done) {
-                // block `done` has landed (this thread's copies; __syncwarp for
-                // the contiguous layout, whose rows the warp copied together)
-                cp_wait<RING - 2>();
-                __syncwarp();
-                const float* raw = RAW + (size_t)(done % RING) * (RAW_BYTES / 4);
+        int64_t inflight = 0;                   // blocks issued (thread 0)
+        if (t == 0)
+            for (int i = 0; i < RING - 1; ++i)
+                if (issue_next((int)(inflight % RING))) ++inflight;
+        // The four converter warps meet at a named barrier once per block, so
+        // none of them leaves the loop early: after a failed wait (`live`
+        // false) they keep iterating without work, every later wait failing
+        // at once on the abort flag.
+        int64_t gc = 0, q = 0, waited = 0;
+        bool live = true;
+        for (int64_t j = 0; j < my_tiles; ++j) {
+            for (int p = 0; p < nb; ++p, ++q) {
+                const int slot = (int)(q % RING);
+                live = live && warp_wait(bar(RAW_FULL + slot), (uint32_t)((q / RING) & 1), abortp, g.status);
+                if (live) waited = q + 1;
+                // this thread's line of the block: [line][32 k] rows of 128 bytes
+                // with 128-byte swizzle (contiguous axis), [32 k][line] (strided)
+                const uint8_t* raw = RAW + (size_t)slot * RAW_BYTES;
                 float v[KB];
+                if (g.contiguous) {
 #pragma unroll
-                for (int k = 0; k < KB; ++k) v[k] = g.inner > 1 ? raw[k * NL + t] : raw[t * RAW_LD + k];
-                __syncwarp();
-                // refill the slot just read
-                if (qj < my_tiles) {
-                    issue_block(qj, qp, (int)(issued % RING));
-                    next_q();
+                    for (int c = 0; c < 8; ++c) {
+                        const float4 w4 = *reinterpret_cast<const float4*>(raw + (size_t)t * 128 +
+                                                                           (size_t)((c ^ (t & 7)) << 4));
+                        v[4 * c] = w4.x;
+                        v[4 * c + 1] = w4.y;
+                        v[4 * c + 2] = w4.z;
+                        v[4 * c + 3] = w4.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < KB; ++k) v[k] = reinterpret_cast<const float*>(raw)[k * NL + t];
                 }
-                cp_commit();
-                ++issued;
+                // every converter has read the slot: thread 0 refills it
+                group_sync(2);
+                if (t == 0 && live && issue_next((int)(inflight % RING))) ++inflight;
                 float mx = 0.0f;
 #pragma unroll
                 for (int k = 0; k < KB; ++k) mx = fmaxf(mx, fabsf(v[k]));
                 const Grids gr = grids_for(mx);
-                for (int h2 = 0; h2 < 2; ++h2) {
-                    if (2 * p + h2 >= nc) break;
+                for (int h2 = 0; h2 < 2; ++h2, ++gc) {
                     const int s = (int)(gc % STAGES);
-                    bool w = true;
                     if (gc >= STAGES)
-                        w = wait_bar(bar(EMPTY + s), (uint32_t)((gc / STAGES - 1) & 1), abortp, g.status);
-                    if (!__all_sync(0xFFFFFFFFu, w)) {
-                        ok = false;
-                        break;
-                    }
+                        live = live && warp_wait(bar(EMPTY + s), (uint32_t)((gc / STAGES - 1) & 1), abortp,
+                                                 g.status);
+                    if (!live) continue;
                     uint8_t* row = sm + (size_t)s * STAGE_BYTES + 3 * PLANE + (size_t)t * 32;
 #pragma unroll
                     for (int qq = 0; qq < 2; ++qq) {
@@ -455,21 +482,37 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc16(const __grid_constant__ CUt
                     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                     __syncwarp();
                     if (lane == 0) mbar_arrive(bar(CVT_FULL + s));
-                    ++gc;
                 }
             }
         }
-        cp_wait<0>();     // no copy outlives the CTA
+        // the field copies still in flight land before the CTA ends
+        if (t == 0)
+            for (int64_t b = waited; b < inflight; ++b)
+                drain_bar(bar(RAW_FULL + (int)(b % RING)), (uint32_t)((b / RING) & 1), g.status);
     } else {
         // ---- epilogue (128 threads): lane quarter q of tensor memory ----
-        const int q = warp & 3, ew = warp - 6;
-        const uint32_t lrow = (uint32_t)(32 * q) << 16;
+        const int qd = warp & 3, et = tid - 192;
+        const uint32_t lrow = (uint32_t)(32 * qd) << 16;
         const uint32_t X = tmem + lrow + 256u, S = tmem + lrow + 384u;
+        const int r = 32 * qd + lane;           // this thread's output row of the tile
         int64_t gb = 0;
+        bool cin_pending = false;
         for (int64_t j = 0; j < my_tiles; ++j) {
-            int mt;
-            int64_t l0;
-            tile_of(j, mt, l0);
+            const TileAt t = tile_of(j);
+            // the tile's Cin into the output tile, once the previous tile's
+            // store has read it
+            if (et == 0) {
+                asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+                mbar_expect_tx(bar(CIN_FULL), OB_BYTES);
+                if (g.contiguous) {
+                    tma_load2(obase, &mcin, bar(CIN_FULL), t.mt * BM, t.l0);
+                } else {
+                    for (int c = 0; c < 4; ++c)
+                        tma_load3(obase + (uint32_t)c * (OB_BYTES / 4), &mcin, bar(CIN_FULL), t.i0 + 32 * c,
+                                  t.mt * BM, t.o);
+                }
+                cin_pending = true;
+            }
             bool ok = true;
             // S = sum of the blocks' L0, each added as soon as it completes
             for (int p = 0; p < nb; ++p, ++gb) {
@@ -494,89 +537,59 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc16(const __grid_constant__ CUt
                 __syncwarp();
                 if (lane == 0) mbar_arrive(bar(BLK_EMPTY + slot));
             }
-            // the last block's commit covered every MMA of the tile (X too);
+            if (ok) ok = warp_wait(bar(CIN_FULL), (uint32_t)(j & 1), abortp, g.status);
             // all four warps leave together if one gave up
             if (!group_and(1, ok)) break;
+            cin_pending = false;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            // S + X of this thread's row into the output tile: [line][row] on
-            // contiguous axes, [row][line] on strided ones
-            const int r = 32 * q + lane;
+            // output tile += S + X: [line][row] (contiguous axis, rows of 512
+            // bytes) or four [row][32 lines] blocks with 128-byte swizzle
             for (int pc = 0; pc < NL / 32; ++pc) {
                 uint32_t a[32], b[32];
                 tmem_ld32(S + (uint32_t)(32 * pc), a);
                 tmem_ld32(X + (uint32_t)(32 * pc), b);
                 asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                if (g.contiguous) {
 #pragma unroll
-                for (int jj = 0; jj < 32; ++jj) {
-                    const float val = __uint_as_float(a[jj]) + __uint_as_float(b[jj]);
-                    if (g.inner == 1) OB[(32 * pc + jj) * OB_LD + r] = val;
-                    else OB[r * OB_LD + 32 * pc + jj] = val;
+                    for (int jj = 0; jj < 32; ++jj) {
+                        float* o = OB + (size_t)(32 * pc + jj) * BM + r;
+                        *o += __uint_as_float(a[jj]) + __uint_as_float(b[jj]);
+                    }
+                } else {
+                    uint8_t* blk = reinterpret_cast<uint8_t*>(OB) + (size_t)pc * (OB_BYTES / 4) + (size_t)r * 128;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        float4* o = reinterpret_cast<float4*>(blk + (size_t)((c ^ (r & 7)) << 4));
+                        float4 w4 = *o;
+                        w4.x += __uint_as_float(a[4 * c]) + __uint_as_float(b[4 * c]);
+                        w4.y += __uint_as_float(a[4 * c + 1]) + __uint_as_float(b[4 * c + 1]);
+                        w4.z += __uint_as_float(a[4 * c + 2]) + __uint_as_float(b[4 * c + 2]);
+                        w4.w += __uint_as_float(a[4 * c + 3]) + __uint_as_float(b[4 * c + 3]);
+                        *o = w4;
+                    }
                 }
             }
             // X and S are free for the next tile
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(bar(ACC_EMPTY));
+            // the output tile's writes reach the TMA (async proxy), then Y
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             group_sync(1);
-            // Y = Cin + sum, coalesced: contiguous axes walk lines (the rows of
-            // the tile are consecutive words), strided axes walk rows.  Each
-            // warp takes every fourth line (row) in batches of 16, so that 64
-            // loads of Cin per lane are in flight at once.
-            constexpr int WB = 16;
-            if (g.inner == 1) {
-                for (int b0 = 0; b0 < NL / 4; b0 += WB) {
-                    float cin[WB][4];
-#pragma unroll
-                    for (int u = 0; u < WB; ++u) {
-                        const int64_t lg = l0 + ew + 4 * (b0 + u);
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const int m = mt * BM + 32 * i + lane;
-                            cin[u][i] = (lg < g.nlines && m < g.Mout) ? g.Cin[lg * g.Mout + m] : 0.0f;
-                        }
-                    }
-#pragma unroll
-                    for (int u = 0; u < WB; ++u) {
-                        const int ll = ew + 4 * (b0 + u);
-                        const int64_t lg = l0 + ll;
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const int m = mt * BM + 32 * i + lane;
-                            if (lg < g.nlines && m < g.Mout)
-                                g.Y[lg * g.Mout + m] = cin[u][i] + OB[ll * OB_LD + 32 * i + lane];
-                        }
-                    }
+            if (et == 0) {
+                if (g.contiguous) {
+                    tma_store2(&my, obase, t.mt * BM, t.l0);
+                } else {
+                    for (int c = 0; c < 4; ++c)
+                        tma_store3(&my, obase + (uint32_t)c * (OB_BYTES / 4), t.i0 + 32 * c, t.mt * BM, t.o);
                 }
-            } else {
-                int64_t ob[4];
-                bool ov[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int64_t lg = l0 + 32 * i + lane;
-                    ov[i] = lg < g.nlines;
-                    ob[i] = ov[i] ? (lg / g.inner) * (int64_t)g.Mout * g.inner + (lg % g.inner) : 0;
-                }
-                for (int b0 = 0; b0 < BM / 4; b0 += WB) {
-                    float cin[WB][4];
-#pragma unroll
-                    for (int u = 0; u < WB; ++u) {
-                        const int m = mt * BM + ew + 4 * (b0 + u);
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            cin[u][i] = (ov[i] && m < g.Mout) ? g.Cin[ob[i] + (int64_t)m * g.inner] : 0.0f;
-                    }
-#pragma unroll
-                    for (int u = 0; u < WB; ++u) {
-                        const int rr = ew + 4 * (b0 + u);
-                        const int m = mt * BM + rr;
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            if (ov[i] && m < g.Mout)
-                                g.Y[ob[i] + (int64_t)m * g.inner] = cin[u][i] + OB[rr * OB_LD + 32 * i + lane];
-                    }
-                }
+                asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
             }
-            group_sync(1);      // the output tile is read before the next one overwrites it
+        }
+        if (et == 0) {
+            // every store has completed, and no Cin load is left in flight
+            asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+            if (cin_pending) drain_bar(bar(CIN_FULL), (uint32_t)((my_tiles - 1) & 1), g.status);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -663,7 +676,36 @@ cudaError_t tc16_set_smem() {
 
 size_t tc16_smem_bytes() { return SMEM; }
 
-cudaError_t tc16_launch(const CUtensorMap& map, const Tc16Gemm& g, cudaStream_t st) {
+int tc16_field_map(float* base, int contiguous, int64_t len, int64_t lines_or_inner, int64_t outer, int64_t pitch,
+                   int ymap, CUtensorMap* map) {
+    EncodeTiled enc = encoder();
+    if (!enc) return -1;
+    CUresult r;
+    const cuuint32_t e2[2] = {1, 1}, e3[3] = {1, 1, 1};
+    if (contiguous) {
+        // rows of `len` values, `pitch` apart; X: 32 k x 128 lines with
+        // 128-byte swizzle; Y: 128 rows x 128 lines
+        const cuuint64_t dims[2] = {(cuuint64_t)len, (cuuint64_t)lines_or_inner};
+        const cuuint64_t strides[1] = {(cuuint64_t)pitch * 4};
+        const cuuint32_t box[2] = {ymap ? (cuuint32_t)BM : (cuuint32_t)KB, (cuuint32_t)NL};
+        r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, e2, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                ymap ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        // (inner, position along the axis, outer); X: 128 lines x 32 k;
+        // Y: 32 lines x 128 rows with 128-byte swizzle (four per tile)
+        const cuuint64_t dims[3] = {(cuuint64_t)lines_or_inner, (cuuint64_t)len, (cuuint64_t)outer};
+        const cuuint64_t strides[2] = {(cuuint64_t)lines_or_inner * 4, (cuuint64_t)(len * lines_or_inner) * 4};
+        const cuuint32_t box[3] = {ymap ? 32u : (cuuint32_t)NL, ymap ? (cuuint32_t)BM : (cuuint32_t)KB, 1};
+        r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, e3, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                ymap ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    return r == CUDA_SUCCESS ? 0 : -1;
+}
+
+cudaError_t tc16_launch(const CUtensorMap& mop, const CUtensorMap& mx, const CUtensorMap& mcin, const CUtensorMap& my,
+                        const Tc16Gemm& g, cudaStream_t st) {
     static thread_local int dev_cached = -1, nsm = 0;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -673,10 +715,10 @@ cudaError_t tc16_launch(const CUtensorMap& map, const Tc16Gemm& g, cudaStream_t 
         if (e != cudaSuccess) return e;
         dev_cached = dev;
     }
-    const int64_t tiles = (g.nlines + NL - 1) / NL * g.MT;
+    const int64_t tiles = g.tiles * g.MT;
     const int64_t grid = tiles < nsm ? tiles : nsm;      // persistent: at most one CTA per SM
     if (grid <= 0) return cudaSuccess;
-    k_tc16<<<(unsigned)grid, THREADS, SMEM, st>>>(map, g);
+    k_tc16<<<(unsigned)grid, THREADS, SMEM, st>>>(mop, mx, mcin, my, g);
     return cudaGetLastError();
 }
 

@@ -12,15 +12,16 @@ namespace pstd {
 
 // One dense derivative applied to every line of an axis:
 //     Y[line, m] = Cin[line, m] + sum_k D[m, k] X[line, k]
-// with line l at (o, i) = (l / inner, l % inner) and element (l, k) of a field
-// of length `len` along the axis at  o * len * inner + k * inner + i.
+// over fields in the plan's padded layout, read and written through tensor
+// maps (tc16_field_map).  Lines come in tiles of 128: on the contiguous (last)
+// axis consecutive rows; on a strided axis 128 consecutive inner indices of
+// one outer block (tpo tiles per outer block).
 struct Tc16Gemm {
     int K, Mout;          // input and output lengths along the axis
     int MT, KC;           // 128-row output tiles, 16-wide k chunks (an even count)
-    int64_t nlines, inner;
-    const float* X;
-    const float* Cin;
-    float* Y;
+    int contiguous;       // 1: the axis is the last one (lines are rows)
+    int64_t tiles;        // line tiles
+    int64_t tpo;          // strided axes: line tiles per outer block
     int* status;          // set to 1 when a bounded wait gives up
 };
 
@@ -31,7 +32,14 @@ struct Tc16Gemm {
 // when the driver's tensor-map encoder is unavailable.
 int tc16_operator(const std::vector<double>& D, int Mout, int K, uint16_t** planes, CUtensorMap* map);
 int tc16_chunks(int K);
-cudaError_t tc16_launch(const CUtensorMap& map, const Tc16Gemm& g, cudaStream_t st);
+// Tensor map of a padded FP32 field for one axis: contiguous (last) axis: rows
+// of `len` values `pitch` floats apart, `lines_or_inner` rows; strided axis:
+// (inner, len, outer) with inner = lines_or_inner (a multiple of 4).  ymap:
+// the output-tile box (Y / Cin), else the field-block box (X).  0 or -1.
+int tc16_field_map(float* base, int contiguous, int64_t len, int64_t lines_or_inner, int64_t outer, int64_t pitch,
+                   int ymap, CUtensorMap* map);
+cudaError_t tc16_launch(const CUtensorMap& mop, const CUtensorMap& mx, const CUtensorMap& mcin, const CUtensorMap& my,
+                        const Tc16Gemm& g, cudaStream_t st);
 cudaError_t tc16_set_smem();
 size_t tc16_smem_bytes();
 
