@@ -125,7 +125,6 @@ struct Axis {
     // BF16 three-way split form on tcgen05: the two operators' BF16 slices
     // (D1: N x lp, D2: lp x N) and their TMA tensor maps
     uint16_t* d_tc16[2] = {nullptr, nullptr};
-    CUtensorMap tc16_map[2];
     int tc16_MT[2] = {0, 0}, tc16_KC[2] = {0, 0};
     // the padded fields along this axis: X maps of p and u_a, Y (and Cin)
     // maps of u_a, p and the accumulator; line tiles
@@ -932,9 +931,7 @@ int build_axis(pstd_plan_s* P, int i) {
         const std::vector<double> D2 = dense_operator64(a, 1, scales[OP_STEP_U]);   // lp x nu
         const int dims[2][2] = {{a.nu, a.lp}, {a.lp, a.nu}};
         for (int o = 0; o < 2; ++o) {
-            const int r = pstd::tc16_operator(o == 0 ? D1 : D2, dims[o][0], dims[o][1], &a.d_tc16[o],
-                                              &a.tc16_map[o]);
-            if (r == -1) return cuda_fail(cudaErrorNotSupported, "cuTensorMapEncodeTiled");
+            const int r = pstd::tc16_operator(o == 0 ? D1 : D2, dims[o][0], dims[o][1], &a.d_tc16[o]);
             if (r != 0) return cuda_fail((cudaError_t)r, "BF16 operator slices");
             a.tc16_MT[o] = (dims[o][0] + 127) / 128;
             a.tc16_KC[o] = pstd::tc16_chunks(dims[o][1]);
@@ -1207,12 +1204,14 @@ int launch_step(pstd_plan_s* P, float* p, float* const* u, int64_t* launches) {
             pstd::Tc16Gemm g1{};
             g1.K = A.lp; g1.Mout = A.nu; g1.MT = A.tc16_MT[0]; g1.KC = A.tc16_KC[0];
             g1.contiguous = contig; g1.tiles = A.tc16_tiles; g1.tpo = A.tc16_tpo; g1.status = status;
-            CK(pstd::tc16_launch(A.tc16_map[0], A.tc16_x[0], A.tc16_y[0], A.tc16_y[0], g1, P->stream));
+            g1.op = (const uint8_t*)A.d_tc16[0];
+            CK(pstd::tc16_launch(A.tc16_x[0], A.tc16_y[0], A.tc16_y[0], g1, P->stream));
             pstd::Tc16Gemm g2 = g1;
             g2.K = A.nu; g2.Mout = A.lp; g2.MT = A.tc16_MT[1]; g2.KC = A.tc16_KC[1];
+            g2.op = (const uint8_t*)A.d_tc16[1];
             const CUtensorMap& cin = (a == P->ndim - 1) ? A.tc16_y[1] : A.tc16_y[2];
             const CUtensorMap& out = (a == 0) ? A.tc16_y[1] : A.tc16_y[2];
-            CK(pstd::tc16_launch(A.tc16_map[1], A.tc16_x[1], cin, out, g2, P->stream));
+            CK(pstd::tc16_launch(A.tc16_x[1], cin, out, g2, P->stream));
             *launches += 2;
             continue;
         }

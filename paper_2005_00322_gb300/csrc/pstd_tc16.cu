@@ -37,8 +37,9 @@
 // Persistent kernel, one CTA per SM, walking (line tile, output tile) pairs:
 // a tile is 128 output rows (MMA M) x 128 lines (MMA N); the MMAs run on
 // 16-wide k chunks.
-//   warp 0      TMA producer: the chunk's three operator slices, one 3-D box of
-//               16 k x 128 rows x 3 slices, 32-byte swizzle;
+//   warp 0      producer: the chunk's three operator slices, one contiguous
+//               12 KB bulk copy (the host stores the operator tiled and
+//               swizzled exactly as the MMA reads it);
 //   warp 1      allocates tensor memory; one thread issues the 6 MMAs of each
 //               chunk and commits them to the stage's mbarrier and, at the
 //               end of a block, to the block's accumulator mbarrier;
@@ -68,8 +69,8 @@ constexpr int BM = 128;                        // output rows per tile (MMA M)
 constexpr int NL = 128;                        // lines per tile (MMA N)
 constexpr int BK = 16;                         // k per MMA chunk: one 32-byte swizzle row of BF16
 constexpr int KB = 32;                         // k per scale block (two chunks)
-constexpr int STAGES = 3;
-constexpr int RING = 4;                        // field blocks in shared memory (three in flight)
+constexpr int STAGES = 4;
+constexpr int RING = 3;                        // field blocks in shared memory (two in flight)
 constexpr uint32_t PLANE = BM * BK * 2;        // one BF16 slice of one chunk: 4 KB
 constexpr uint32_t STAGE_BYTES = 6 * PLANE;    // operator Dh Dm Dl, field Xh Xm Xl
 constexpr uint32_t RAW_BYTES = NL * KB * 4;    // one FP32 field block: 16 KB
@@ -142,6 +143,13 @@ __device__ __forceinline__ bool group_and(int id, bool v) {
 }
 __device__ __forceinline__ void group_sync(int id) { asm volatile("bar.sync %0, 128;\n" ::"r"(id) : "memory"); }
 
+// Contiguous bulk copy (16-byte aligned, size a multiple of 16) into this
+// CTA's shared memory, completing on an mbarrier.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+                 "l"((uint64_t)src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
 // TMA tile loads into this CTA's shared memory, completing on an mbarrier.
 __device__ __forceinline__ void tma_load2(uint32_t dst, const CUtensorMap* m, uint32_t bar, int c0, int c1) {
     asm volatile(
@@ -248,8 +256,8 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 #endif
 
 __global__ void __launch_bounds__(THREADS, 1)
-    k_tc16(const __grid_constant__ CUtensorMap mop, const __grid_constant__ CUtensorMap mx,
-           const __grid_constant__ CUtensorMap mcin, const __grid_constant__ CUtensorMap my, const Tc16Gemm g) {
+    k_tc16(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mcin,
+           const __grid_constant__ CUtensorMap my, const Tc16Gemm g) {
 #ifdef __CUDA_ARCH__
     extern __shared__ uint8_t tc16_raw[];
     __shared__ __align__(8) uint64_t bars[3 * STAGES + RING + 7];
@@ -310,7 +318,6 @@ __global__ void __launch_bounds__(THREADS, 1)
         mbar_init(bar(CIN_FULL), 1);
         mbar_init(bar(FINAL), 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];\n" ::"l"((uint64_t)&mop) : "memory");
         asm volatile("prefetch.tensormap [%0];\n" ::"l"((uint64_t)&mx) : "memory");
         asm volatile("prefetch.tensormap [%0];\n" ::"l"((uint64_t)&mcin) : "memory");
         asm volatile("prefetch.tensormap [%0];\n" ::"l"((uint64_t)&my) : "memory");
@@ -343,7 +350,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                         break;
                     }
                     mbar_expect_tx(bar(TMA_FULL + s), 3 * PLANE);
-                    tma_load3(sbase + (uint32_t)s * STAGE_BYTES, &mop, bar(TMA_FULL + s), c * BK, t.mt * BM, 0);
+                    bulk_load(sbase + (uint32_t)s * STAGE_BYTES, g.op + ((size_t)t.mt * nc + c) * (3 * PLANE),
+                              3 * PLANE, bar(TMA_FULL + s));
                     issued[s] = (int)(n + 1);
                 }
             }
@@ -630,10 +638,11 @@ uint16_t bf16_exact(double x) {
 
 }  // namespace
 
-int tc16_operator(const std::vector<double>& D, int Mout, int K, uint16_t** planes, CUtensorMap* map) {
-    const int Mpad = (Mout + BM - 1) / BM * BM, Kpad = (K + KB - 1) / KB * KB;
-    const size_t P = (size_t)Mpad * Kpad;
-    std::vector<uint16_t> h(3 * P, 0);
+int tc16_operator(const std::vector<double>& D, int Mout, int K, uint16_t** planes) {
+    const int MT = (Mout + BM - 1) / BM, KC = tc16_chunks(K);
+    // per (row, 32-wide k block): E with 2^E > the block's maximum, then three
+    // slices on the grids 2^(E-8), 2^(E-16), 2^(E-24)
+    std::vector<uint16_t> h((size_t)MT * KC * 3 * PLANE / 2, 0);
     for (int m = 0; m < Mout; ++m)
         for (int k0 = 0; k0 < K; k0 += KB) {
             const int k1 = k0 + KB < K ? k0 + KB : K;
@@ -644,10 +653,15 @@ int tc16_operator(const std::vector<double>& D, int Mout, int K, uint16_t** plan
             std::frexp(mx, &E);                        // 2^E > mx
             for (int k = k0; k < k1; ++k) {
                 double r = D[(size_t)m * K + k];
+                // the chunk's 12 KB as the MMA reads it: [slice][row][32 bytes],
+                // each row's 16-byte halves swapped when bit 2 of the row is set
+                const int mt = m / BM, rr = m % BM, kc = k / BK, kk = k % BK;
+                const size_t blk = ((size_t)mt * KC + kc) * (3 * PLANE);
+                const size_t in = (size_t)rr * 32 + (size_t)(((kk >> 3) ^ ((rr >> 2) & 1)) << 4) + (size_t)(kk & 7) * 2;
                 for (int p = 0; p < 3; ++p) {
                     const double gp = std::ldexp(1.0, E - 8 - 8 * p);
                     const double a = std::nearbyint(r / gp) * gp;
-                    h[(size_t)p * P + (size_t)m * Kpad + k] = bf16_exact(a);
+                    h[(blk + (size_t)p * PLANE + in) / 2] = bf16_exact(a);
                     r -= a;
                 }
             }
@@ -655,17 +669,7 @@ int tc16_operator(const std::vector<double>& D, int Mout, int K, uint16_t** plan
     cudaError_t e = cudaMalloc((void**)planes, h.size() * sizeof(uint16_t));
     if (e != cudaSuccess) return (int)e;
     e = cudaMemcpy(*planes, h.data(), h.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return (int)e;
-    EncodeTiled enc = encoder();
-    if (!enc) return -1;
-    const cuuint64_t dims[3] = {(cuuint64_t)Kpad, (cuuint64_t)Mpad, 3};
-    const cuuint64_t strides[2] = {(cuuint64_t)Kpad * 2, (cuuint64_t)P * 2};
-    const cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)BM, 3};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, *planes, dims, strides, box, estr,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
-                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? 0 : -1;
+    return (int)e;
 }
 
 int tc16_chunks(int K) { return (K + KB - 1) / KB * (KB / BK); }
@@ -704,8 +708,8 @@ int tc16_field_map(float* base, int contiguous, int64_t len, int64_t lines_or_in
     return r == CUDA_SUCCESS ? 0 : -1;
 }
 
-cudaError_t tc16_launch(const CUtensorMap& mop, const CUtensorMap& mx, const CUtensorMap& mcin, const CUtensorMap& my,
-                        const Tc16Gemm& g, cudaStream_t st) {
+cudaError_t tc16_launch(const CUtensorMap& mx, const CUtensorMap& mcin, const CUtensorMap& my, const Tc16Gemm& g,
+                        cudaStream_t st) {
     static thread_local int dev_cached = -1, nsm = 0;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -718,7 +722,7 @@ cudaError_t tc16_launch(const CUtensorMap& mop, const CUtensorMap& mx, const CUt
     const int64_t tiles = g.tiles * g.MT;
     const int64_t grid = tiles < nsm ? tiles : nsm;      // persistent: at most one CTA per SM
     if (grid <= 0) return cudaSuccess;
-    k_tc16<<<(unsigned)grid, THREADS, SMEM, st>>>(mop, mx, mcin, my, g);
+    k_tc16<<<(unsigned)grid, THREADS, SMEM, st>>>(mx, mcin, my, g);
     return cudaGetLastError();
 }
 

@@ -22,15 +22,17 @@ struct Tc16Gemm {
     int contiguous;       // 1: the axis is the last one (lines are rows)
     int64_t tiles;        // line tiles
     int64_t tpo;          // strided axes: line tiles per outer block
+    const uint8_t* op;    // the operator's slices, tiled (tc16_operator)
     int* status;          // set to 1 when a bounded wait gives up
 };
 
-// The operator D (Mout x K, FP64) as three BF16 planes [Mpad][Kpad] on the
-// device, split per (row, 32-wide k block) so that the main product's block
-// sums are exact (pstd_tc16.cu); `planes` receives the device buffer (owned by
-// the caller) and `map` its TMA tensor map.  Returns a cudaError_t value, or -1
-// when the driver's tensor-map encoder is unavailable.
-int tc16_operator(const std::vector<double>& D, int Mout, int K, uint16_t** planes, CUtensorMap* map);
+// The operator D (Mout x K, FP64) as three BF16 slices per (row, 32-wide k
+// block) power-of-two grid, so that the main product's block sums are exact
+// (pstd_tc16.cu), stored on the device chunk by chunk: for output tile mt and
+// 16-wide chunk c, 12 KB at (mt * chunks + c) * 12 KB laid out as the MMA
+// reads them ([slice][128 rows][16 k], 32-byte swizzle).  `planes` receives
+// the device buffer (owned by the caller).  Returns a cudaError_t value.
+int tc16_operator(const std::vector<double>& D, int Mout, int K, uint16_t** planes);
 int tc16_chunks(int K);
 // Tensor map of a padded FP32 field for one axis: contiguous (last) axis: rows
 // of `len` values `pitch` floats apart, `lines_or_inner` rows; strided axis:
@@ -38,8 +40,8 @@ int tc16_chunks(int K);
 // the output-tile box (Y / Cin), else the field-block box (X).  0 or -1.
 int tc16_field_map(float* base, int contiguous, int64_t len, int64_t lines_or_inner, int64_t outer, int64_t pitch,
                    int ymap, CUtensorMap* map);
-cudaError_t tc16_launch(const CUtensorMap& mop, const CUtensorMap& mx, const CUtensorMap& mcin, const CUtensorMap& my,
-                        const Tc16Gemm& g, cudaStream_t st);
+cudaError_t tc16_launch(const CUtensorMap& mx, const CUtensorMap& mcin, const CUtensorMap& my, const Tc16Gemm& g,
+                        cudaStream_t st);
 cudaError_t tc16_set_smem();
 size_t tc16_smem_bytes();
 
