@@ -167,6 +167,22 @@ typedef struct {
 int pstd_plan_ex(const pstd_desc* desc, void* stream, const pstd_plan_opts* opts,
                  pstd_plan_t** out);
 
+/* pstd_plan_ex with the axis-pass schedules chosen by measurement on the
+ * current device: for the FFT form (form 0, not persistent), each axis in
+ * turn tries every register-FFT schedule (variant x line pairs per CTA, with
+ * 32 to 256 threads per CTA) of its FFT length, timed with CUDA events on
+ * `stream` around graph-replayed runs (96 minus 32 steps) on zero-filled
+ * scratch fields the call allocates and frees; a candidate replaces the
+ * current choice when it is at least 2% faster.  `base` (may be NULL) gives
+ * the starting options; the winner is cached per (device, grid, walls, form)
+ * for the life of the process, so a second call for the same shape returns at
+ * once.  Other forms are built as by pstd_plan_ex.  times_us (may be NULL):
+ * [0] the tuned step time, [1] the default schedule's, in microseconds (-1 if
+ * not tuned).  The tuning is a property of the implementation; the paper has
+ * no counterpart.  Errors: as pstd_plan_ex, PSTD_ENOMEM (scratch). */
+int pstd_plan_autotune(const pstd_desc* desc, void* stream, const pstd_plan_opts* base, pstd_plan_t** out,
+                       double times_us[2]);
+
 /* The schedule a plan chose for `axis`: variant, lanes per sequence,
  * sequences per CTA, CTAs per launch (-1 for an axis on the generic
  * shared-memory FFT or dense path).  Errors: PSTD_EINVAL. */

@@ -22,6 +22,7 @@ ERRORS = {0: "PSTD_OK", -1: "PSTD_EINVAL", -2: "PSTD_EUNSTABLE", -3: "PSTD_ENOME
 SIGNATURES = {
     "pstd_plan": (c_int, [c_void_p, c_void_p, POINTER(c_void_p)]),
     "pstd_plan_ex": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(c_void_p)]),
+    "pstd_plan_autotune": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(c_void_p), POINTER(c_double)]),
     "pstd_plan_schedule": (c_int, [c_void_p, c_int, POINTER(c_int)]),
     "pstd_plan_persistent": (c_int, [c_void_p, POINTER(c_int)]),
     "pstd_field_shape": (c_int, [c_void_p, c_int, POINTER(c_int64)]),

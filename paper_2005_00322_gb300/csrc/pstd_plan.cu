@@ -221,6 +221,7 @@ struct pstd_plan_s {
     pstd_desc desc{};
     pstd_plan_opts opts{{-1, -1, -1}, {-1, -1, -1}, 0, 0, 0, 0};
     unsigned* d_sync = nullptr;       // grid barrier: count, generation, status
+    int nsm = 152;                    // SMs of the plan's device (queried at plan time)
     int persist_ok = 0;
     WLaunch pgeo{};
     cudaStream_t stream = nullptr;
@@ -791,17 +792,18 @@ int build_axis(pstd_plan_s* P, int i) {
     // 4 elements shorten each lane's dependent chain; measured 13.7 -> 12.2 us
     // per 512^2 step and 14.2 -> 9.3 us per 256^2 step (with many lines, as
     // in 256^3, the 8-element schedule stays faster: 0.69 vs 0.94 ms)
-    if (ov < 0 && V == 1 && pstd::wlanes_v3(a.L) > 0 && (a.nlines + 1) / 2 < 2 * 2 * 152) {
+    const int64_t nsm = P->nsm;
+    if (ov < 0 && V == 1 && pstd::wlanes_v3(a.L) > 0 && (a.nlines + 1) / 2 < 2 * 2 * nsm) {
         V = 3;
         T = pstd::wlanes_v3(a.L);
     }
     if (os == 0 || os > 256 || (os > 0 && (os & (os - 1)))) return PSTD_EINVAL;
     const bool auto_os = os < 0;
-    if (os < 0 && V >= 1 && T <= 128 && (a.nlines + 1) / 2 >= 2 * 2 * 152) os = 2;
+    if (os < 0 && V >= 1 && T <= 128 && (a.nlines + 1) / 2 >= 2 * 2 * nsm) os = 2;
     // strided axes stage tiles of 2 os lines: 4 sequences make each staged
     // run 8 words (one 32-byte sector); measured 0.815 -> 0.768 ms per 256^3
     // step.  Not for the persistent run, whose axes share one CTA size.
-    if (auto_os && os == 2 && !P->opts.persistent && inner > 1 && T <= 64 && (a.nlines + 1) / 2 >= 4 * 2 * 152) os = 4;
+    if (auto_os && os == 2 && !P->opts.persistent && inner > 1 && T <= 64 && (a.nlines + 1) / 2 >= 4 * 2 * nsm) os = 4;
     if (a.kind == 0 && T > 0) {
         std::vector<float2> wt;
         if (!wtw(a.L, V, wt)) return PSTD_EUNSUPPORTED;
@@ -862,7 +864,7 @@ int build_axis(pstd_plan_s* P, int i) {
             w.ph = a.d_ph;
         }
         const int64_t nseq = (a.nlines + 1) / 2;
-        const int64_t want = 2 * 152;
+        const int64_t want = 2 * nsm;
         int threads = V >= 1 ? T : 128;
         if (os > 0) {
             threads = os * T;
@@ -973,7 +975,7 @@ int build_axis(pstd_plan_s* P, int i) {
         auto ctas = [&](int gg) {
             return a.inner == 1 ? (a.nlines + gg - 1) / gg : (a.nlines / a.inner) * ((a.inner + gg - 1) / gg);
         };
-        while (G > 8 && ctas(G) < 152) G /= 2;
+        while (G > 8 && ctas(G) < P->nsm) G /= 2;
         g.G = G;
         a.gsmem = pstd::gemm_smem_bytes(G, g.KT1, g.KT2, a.N);
         if (a.inner == 1) a.ggrid = (unsigned)((a.nlines + G - 1) / G);
@@ -1471,6 +1473,12 @@ int pstd_plan_ex(const pstd_desc* desc, void* stream, const pstd_plan_opts* opts
     if (!P) return PSTD_ENOMEM;
     P->desc = *desc;
     if (opts) P->opts = *opts;
+    {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+            P->nsm = n;
+    }
     if (P->opts.form < 0 || P->opts.form > 3) {
         delete P;
         return PSTD_EINVAL;

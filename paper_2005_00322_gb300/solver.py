@@ -43,7 +43,7 @@ class Solver:
 
     def __init__(self, ncells, dx, bc, c0=1500.0, rho0=1000.0, dt=None, cfl=None,
                  uinit="halfstep", device=None, stream=None, schedule=None, form="fft",
-                 persistent=False, spin_limit=0, withhold_arrivals=0):
+                 persistent=False, spin_limit=0, withhold_arrivals=0, autotune=False):
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the PSTD library runs on the GPU only")
         self.lib = _abi.load()
@@ -75,9 +75,19 @@ class Solver:
             opts.spin_limit = int(spin_limit)
             opts.withhold_arrivals = int(withhold_arrivals)
         h = ctypes.c_void_p()
-        rc = self.lib.pstd_plan_ex(ctypes.byref(self._desc), ctypes.c_void_p(self.stream.cuda_stream),
-                                   ctypes.byref(opts) if opts is not None else None, ctypes.byref(h))
-        _abi.check(self.lib, rc, "pstd_plan_ex")
+        # autotune: the axis-pass schedules are measured on the device (pstd_plan_autotune)
+        self.tune_us = None
+        if autotune:
+            times = (ctypes.c_double * 2)()
+            rc = self.lib.pstd_plan_autotune(ctypes.byref(self._desc), ctypes.c_void_p(self.stream.cuda_stream),
+                                             ctypes.byref(opts) if opts is not None else None, ctypes.byref(h),
+                                             times)
+            _abi.check(self.lib, rc, "pstd_plan_autotune")
+            self.tune_us = (times[0], times[1])
+        else:
+            rc = self.lib.pstd_plan_ex(ctypes.byref(self._desc), ctypes.c_void_p(self.stream.cuda_stream),
+                                       ctypes.byref(opts) if opts is not None else None, ctypes.byref(h))
+            _abi.check(self.lib, rc, "pstd_plan_ex")
         self._h = h
         self.shapes = [self.field_shape(f) for f in range(self.ndim + 1)]
 

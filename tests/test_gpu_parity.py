@@ -306,3 +306,29 @@ def test_gpu_energy_drift_plane512():
     e1 = energy_now()
     assert abs(e1 - e0) < 1e-5 * e0
     s.close()
+
+
+@pytest.mark.parametrize("ncells,bcs", [((512, 512), [("D", "D"), ("N", "N")]), ((96, 80, 64), [("N", "D"), ("D", "N"), ("D", "D")])])
+def test_autotuned_plan(ncells, bcs):
+    """pstd_plan_autotune: the tuned schedule is never slower than the default
+    by its own measurement, the choice is cached, and a tuned run matches the
+    default plan's run to the parity tolerance."""
+    from paper_2005_00322_gb300 import Solver
+    a = Solver(ncells, 1e-4, bcs, cfl=0.3, autotune=True)
+    tuned, default = a.tune_us
+    assert 0 < tuned <= default
+    b = Solver(ncells, 1e-4, bcs, cfl=0.3, autotune=True)     # cached: same choice, same times
+    assert b.tune_us == a.tune_us and [b.schedule()] == [a.schedule()]
+    c = Solver(ncells, 1e-4, bcs, cfl=0.3)
+    w = inputs.small(ncells, bcs, nblobs=2)
+    p0 = np.asarray(c.restrict(w.p0_full()), np.float32)
+    outs = []
+    for s in (a, c):
+        p = torch.tensor(p0, device="cuda")
+        us = [torch.zeros(sh, device="cuda") for sh in s.shapes[1:]]
+        s.init_velocity(p, us)
+        s.run(p, us, 100)
+        outs.append(host(p))
+    assert rel_l2(outs[0], outs[1]) < 1e-5
+    for s in (a, b, c):
+        s.close()
