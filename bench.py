@@ -278,14 +278,17 @@ def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> flo
 class SingleRunner:
     """One grid through Solver (pstd_plan / pstd_run)."""
 
-    def __init__(self, w, form="fft", persistent=False):
+    def __init__(self, w, form="fft", persistent=False, autotune=True):
         import torch
         from paper_2005_00322_gb300 import Solver
         self.w = w
         # order2: the second-order pressure-only form (pstd_init_prev / pstd_run2)
         self.order2 = form == "order2"
+        # the FFT form's axis-pass schedules are measured on the device
+        # (pstd_plan_autotune) unless --no-autotune
         self.solver = Solver(w.ncells, w.dx, w.bc, c0=w.c0, rho0=w.rho0, cfl=w.cfl,
-                             form="fft" if self.order2 else form, persistent=persistent)
+                             form="fft" if self.order2 else form, persistent=persistent,
+                             autotune=autotune and not persistent)
         self.stream = self.solver.stream
         p0 = np.asarray(self.solver.restrict(w.p0_full()), np.float32)
         self.p0 = torch.tensor(p0, device="cuda")
@@ -536,6 +539,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--leapfrog-steps", type=int, default=0, help="override the workload's step count")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the plan's default axis-pass schedules (no pstd_plan_autotune)")
     ap.add_argument("--persistent", action="store_true",
                     help="pstd_run as one cooperative kernel with grid barriers")
     ap.add_argument("--form", default="fft", choices=["fft", "split", "split-bf16", "tensor", "order2"],
@@ -574,7 +579,7 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
 
-    run = SingleRunner(w, args.form, args.persistent) if single else BatchRunner(w)
+    run = SingleRunner(w, args.form, args.persistent, not args.no_autotune) if single else BatchRunner(w)
     st = run.stream
     steps_per = members_of(w)[0].steps
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
@@ -721,6 +726,9 @@ def main():
                "l2": "flushed (256 MB write) before each timed bench step",
                "parallelism": "replicas" if world > 1 else "single GPU", "form": args.form,
                "persistent": bool(args.persistent)}
+        if single:
+            cfg["schedule"] = run.solver.schedule()
+            cfg["autotune_us_per_step"] = run.solver.tune_us
         if single:
             cfg["bc"] = ["".join(b) for b in w.bc]
         elif not isinstance(w, list):
