@@ -126,7 +126,11 @@ int pstd_plan(const pstd_desc* desc, void* stream, pstd_plan_t** out);
  * with many lines), variant 1 spreads each FFT over up to 128 lanes (FFT
  * lengths 256, 512, 768, 1024), variant 2 (length 1024) uses 64 lanes of 16
  * elements, variant 3 (lengths 512, 1024) 128 / 256 lanes of 4 elements (the
- * default for those lengths on axes with too few lines to fill the GPU).
+ * default for those lengths on axes with too few lines to fill the GPU),
+ * variant 4 (lengths 256, 512) variant 1's FFT with its coefficient and
+ * twiddle tables read from shared memory instead of registers (fewer
+ * registers per thread, more resident CTAs).  An unavailable variant gives
+ * PSTD_EINVAL.
  * seqs_per_cta: line pairs per CTA (a power of two). */
 typedef struct {
     int variant[3];

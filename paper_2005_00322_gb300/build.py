@@ -23,6 +23,11 @@ LIB = os.path.join(LIBDIR, "libpstd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]
+# The register-FFT pass units write every multiply-add of the pass explicitly
+# (rfma in pstd_ops.cuh); with contraction off, no other product is fused, so
+# the per-axis kernels and the cooperative kernel, which inline the same pass
+# code, round identically.
+NO_CONTRACT = ("pstd_wkernels_",)
 
 
 def nvcc() -> str:
@@ -61,7 +66,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+        own = ["-fmad=false"] if os.path.basename(src).startswith(NO_CONTRACT) else []
+        cmd = [cc, *ARCH, *FLAGS, *own, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")

@@ -77,17 +77,54 @@ struct LineOp {
     FftPlan fft;            // kinds 0 (length L) and 2 (length M2)
 };
 
+// Scalar arithmetic whose rounding is fixed by the source: each product,
+// sum and fused multiply-add below is one IEEE operation that the compiler
+// may neither merge with a neighbour into a fused multiply-add nor split, so a
+// pass inlined into different kernels (the per-axis launches, the
+// cooperative run) rounds identically.  Where a product feeds a sum, the
+// fused form is written out (rfma), so nothing is lost against contraction.
+PSTD_HD float rmul(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fmul_rn(a, b);
+#else
+    return a * b;
+#endif
+}
+PSTD_HD float radd(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fadd_rn(a, b);
+#else
+    return a + b;
+#endif
+}
+PSTD_HD float rsub(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fsub_rn(a, b);
+#else
+    return a - b;
+#endif
+}
+PSTD_HD float rfma(float a, float b, float c) {  // a * b + c, rounded once
+#ifdef __CUDA_ARCH__
+    return __fmaf_rn(a, b, c);
+#else
+    return fmaf(a, b, c);
+#endif
+}
+
 PSTD_HD float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    return make_float2(rfma(a.x, b.x, -rmul(a.y, b.y)), rfma(a.x, b.y, rmul(a.y, b.x)));
 }
 PSTD_HD float2 cmulc(float2 a, float2 b) {  // a * conj(b)
-    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+    return make_float2(rfma(a.x, b.x, rmul(a.y, b.y)), rfma(a.y, b.x, -rmul(a.x, b.y)));
 }
-PSTD_HD float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-PSTD_HD float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-PSTD_HD float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+PSTD_HD float2 cadd(float2 a, float2 b) { return make_float2(radd(a.x, b.x), radd(a.y, b.y)); }
+PSTD_HD float2 csub(float2 a, float2 b) { return make_float2(rsub(a.x, b.x), rsub(a.y, b.y)); }
+PSTD_HD float2 cscale(float2 a, float s) { return make_float2(rmul(a.x, s), rmul(a.y, s)); }
+// a * s + b (real s), each component rounded once
+PSTD_HD float2 cfma(float2 a, float s, float2 b) { return make_float2(rfma(a.x, s, b.x), rfma(a.y, s, b.y)); }
 // multiply by sigma * i, sigma = -1 (forward) or +1 (inverse)
-PSTD_HD float2 cmuli(float2 a, float sigma) { return make_float2(-sigma * a.y, sigma * a.x); }
+PSTD_HD float2 cmuli(float2 a, float sigma) { return make_float2(rmul(-sigma, a.y), rmul(sigma, a.x)); }
 
 // ---- small DFTs: y_k = sum_q a_q exp(sigma 2 pi i q k / R) -----------------
 PSTD_HD void dft2(float2* a) {
@@ -100,7 +137,7 @@ PSTD_HD void dft3(float2* a, float sigma) {
     const float s = 0.86602540378443864676f;  // sqrt(3)/2
     float2 t1 = cadd(a[1], a[2]);
     float2 t2 = cmuli(cscale(csub(a[1], a[2]), s), sigma);
-    float2 m = cadd(a[0], cscale(t1, c));
+    float2 m = cfma(t1, c, a[0]);
     a[0] = cadd(a[0], t1);
     a[1] = cadd(m, t2);
     a[2] = csub(m, t2);
@@ -120,10 +157,10 @@ PSTD_HD void dft5(float2* a, float sigma) {
     const float s2 = 0.58778525229247312917f;   // sin(4 pi / 5)
     float2 t1 = cadd(a[1], a[4]), d1 = csub(a[1], a[4]);
     float2 t2 = cadd(a[2], a[3]), d2 = csub(a[2], a[3]);
-    float2 m1 = cadd(a[0], cadd(cscale(t1, c1), cscale(t2, c2)));
-    float2 m2 = cadd(a[0], cadd(cscale(t1, c2), cscale(t2, c1)));
-    float2 r1 = cmuli(cadd(cscale(d1, s1), cscale(d2, s2)), sigma);
-    float2 r2 = cmuli(csub(cscale(d1, s2), cscale(d2, s1)), sigma);
+    float2 m1 = cadd(a[0], cfma(t1, c1, cscale(t2, c2)));
+    float2 m2 = cadd(a[0], cfma(t1, c2, cscale(t2, c1)));
+    float2 r1 = cmuli(cfma(d1, s1, cscale(d2, s2)), sigma);
+    float2 r2 = cmuli(cfma(d1, s2, cscale(d2, -s1)), sigma);
     a[0] = cadd(a[0], cadd(t1, t2));
     a[1] = cadd(m1, r1);
     a[4] = csub(m1, r1);

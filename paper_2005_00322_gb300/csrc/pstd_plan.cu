@@ -775,7 +775,11 @@ int build_axis(pstd_plan_s* P, int i) {
     int V = 0;
     int os = P->opts.seqs_per_cta[i];
     const int ov = P->opts.variant[i];
-    if (ov == 3) {
+    if (ov == 4) {
+        if (pstd::wlanes_v4(a.L) == 0) return PSTD_EINVAL;
+        V = 4;
+        T = pstd::wlanes_v4(a.L);
+    } else if (ov == 3) {
         if (pstd::wlanes_v3(a.L) == 0) return PSTD_EINVAL;
         V = 3;
         T = pstd::wlanes_v3(a.L);

@@ -264,10 +264,11 @@ PSTD_HD void derivative(float2 (&v)[S::E], int t, float2* sm, const WAxis& A, co
 }
 
 // Schedules whose lanes hold at most 8 elements keep their tables in
-// registers; the others stage them in shared memory.
+// registers (except V = 4, which trades them for occupancy); the others
+// stage them in shared memory.
 template <class S>
 constexpr bool reg_tables() {
-    return S::V >= 1 && S::E <= 8;
+    return S::V >= 1 && S::V != 4 && S::E <= 8;
 }
 
 // Tables of one derivative for schedule S (registers for the latency

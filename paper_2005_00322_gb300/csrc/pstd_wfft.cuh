@@ -117,7 +117,8 @@ struct Dft {
 // V = 0 (throughput): many elements per lane, few passes, for axes with many
 // lines.  V = 1 (latency): 8 elements per lane spread over up to 128 lanes,
 // for axes with too few lines to fill the GPU, where one sequence's latency
-// sets the pass time.  A sequence wider than a warp exchanges through a CTA
+// sets the pass time.  V = 4: the radices of V = 1 with the tables read from
+// shared memory instead of registers (fewer registers, more resident CTAs).  A sequence wider than a warp exchanges through a CTA
 // barrier.
 template <int L, int V = 0>
 struct Sched;
@@ -149,6 +150,8 @@ PSTD_SCHED(1024, 2, 64, 16, 16, 4)
 PSTD_SCHED(768, 1, 64, 4, 4, 4, 4, 3)
 PSTD_SCHED(1024, 3, 256, 4, 4, 4, 4, 4)
 PSTD_SCHED(512, 3, 128, 4, 4, 4, 4, 2)
+PSTD_SCHED(256, 4, 32, 8, 8, 4)
+PSTD_SCHED(512, 4, 64, 8, 8, 8)
 #undef PSTD_SCHED
 
 // Ns before pass p (product of earlier radices)

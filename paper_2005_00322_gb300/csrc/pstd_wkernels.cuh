@@ -10,10 +10,18 @@
 
 namespace pstd {
 
+// Resident CTAs of 256 threads per SM that a pass kernel is compiled for:
+// the latency passes of the 3-D sizes (L <= 768) run at 128 registers, their
+// shared-table form (V = 4) at 80.
+template <int L, int V>
+constexpr int wmin_blocks() {
+    return V == 4 ? 3 : (V == 1 && L <= 768) ? 2 : 1;
+}
+
 // The contiguous latency pass of the 3-D sizes (L <= 768, the lean form of
 // step_contig) also runs at 128 registers.
 template <int L, int V>
-__global__ void __launch_bounds__(256, (V == 1 && L <= 768) ? 2 : 1) k_wstep_c(WStep a) {
+__global__ void __launch_bounds__(256, wmin_blocks<L, V>()) k_wstep_c(WStep a) {
     extern __shared__ float4 wsm4[];  // 16-byte aligned for cp.async
     float2* wsm = (float2*)wsm4;
     wk::step_contig<wf::Sched<L, V>>(a, blockIdx.x, wsm, threadIdx.x, blockDim.x);
@@ -21,7 +29,7 @@ __global__ void __launch_bounds__(256, (V == 1 && L <= 768) ? 2 : 1) k_wstep_c(W
 // The strided latency pass of the 3-D sizes (L <= 768) runs at 128 registers,
 // 4 CTAs of 128 threads per SM (a few bytes of spill), for occupancy.
 template <int L, int V>
-__global__ void __launch_bounds__(256, (V == 1 && L <= 768) ? 2 : 1) k_wstep_s(WStep a) {
+__global__ void __launch_bounds__(256, wmin_blocks<L, V>()) k_wstep_s(WStep a) {
     extern __shared__ float4 wsm4[];  // 16-byte aligned for cp.async
     float2* wsm = (float2*)wsm4;
     wk::step_strided<wf::Sched<L, V>>(a, blockIdx.x, wsm, threadIdx.x, blockDim.x);
@@ -126,35 +134,38 @@ void wtwiddles(std::vector<float2>& out) {
 }
 
 // Dispatch over the (length, variant) pairs one translation unit
-// instantiates; the key is 2 L + V.
+// instantiates; the key is 8 L + V.
 #define PSTD_WDISPATCH(NAME, LIST)                                                                        \
     cudaError_t NAME##_step(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WStep& a) {   \
-        switch (2 * L + V) { LIST(PSTD_WCASE_STEP) default: return cudaErrorInvalidValue; }              \
+        switch (8 * L + V) { LIST(PSTD_WCASE_STEP) default: return cudaErrorInvalidValue; }              \
     }                                                                                                    \
     cudaError_t NAME##_grad(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WGrad& a) {   \
-        switch (2 * L + V) { LIST(PSTD_WCASE_GRAD) default: return cudaErrorInvalidValue; }              \
+        switch (8 * L + V) { LIST(PSTD_WCASE_GRAD) default: return cudaErrorInvalidValue; }              \
     }                                                                                                    \
     cudaError_t NAME##_smem(int L, int V, int bytes) {                                                   \
-        switch (2 * L + V) { LIST(PSTD_WCASE_SMEM) default: return cudaErrorInvalidValue; }              \
+        switch (8 * L + V) { LIST(PSTD_WCASE_SMEM) default: return cudaErrorInvalidValue; }              \
     }                                                                                                    \
     bool NAME##_twiddles(int L, int V, std::vector<float2>& out) {                                       \
-        switch (2 * L + V) { LIST(PSTD_WCASE_TW) default: return false; }                                \
+        switch (8 * L + V) { LIST(PSTD_WCASE_TW) default: return false; }                                \
     }                                                                                                    \
     cudaError_t NAME##_persist(int L, int V, const WLaunch& g, cudaStream_t st, const PersistArgs& a) {  \
-        switch (2 * L + V) { LIST(PSTD_WCASE_PERSIST) default: return cudaErrorInvalidValue; }           \
+        switch (8 * L + V) { LIST(PSTD_WCASE_PERSIST) default: return cudaErrorInvalidValue; }           \
     }                                                                                                    \
     cudaError_t NAME##_persist_blocks(int L, int V, int threads, size_t smem, int* blocks) {             \
-        switch (2 * L + V) { LIST(PSTD_WCASE_PBLOCKS) default: return cudaErrorInvalidValue; }           \
+        switch (8 * L + V) { LIST(PSTD_WCASE_PBLOCKS) default: return cudaErrorInvalidValue; }           \
     }
-#define PSTD_WCASE_STEP(LL, VV) case 2 * LL + VV: return wlaunch_step<LL, VV>(s, g, st, a);
-#define PSTD_WCASE_GRAD(LL, VV) case 2 * LL + VV: return wlaunch_grad<LL, VV>(s, g, st, a);
-#define PSTD_WCASE_SMEM(LL, VV) case 2 * LL + VV: return wset_smem<LL, VV>(bytes);
-#define PSTD_WCASE_TW(LL, VV) case 2 * LL + VV: wtwiddles<LL, VV>(out); return true;
-#define PSTD_WCASE_PERSIST(LL, VV) case 2 * LL + VV: return wlaunch_persist<LL, VV>(g, st, a);
-#define PSTD_WCASE_PBLOCKS(LL, VV) case 2 * LL + VV: return wpersist_blocks<LL, VV>(threads, smem, blocks);
+#define PSTD_WCASE_STEP(LL, VV) case 8 * LL + VV: return wlaunch_step<LL, VV>(s, g, st, a);
+#define PSTD_WCASE_GRAD(LL, VV) case 8 * LL + VV: return wlaunch_grad<LL, VV>(s, g, st, a);
+#define PSTD_WCASE_SMEM(LL, VV) case 8 * LL + VV: return wset_smem<LL, VV>(bytes);
+#define PSTD_WCASE_TW(LL, VV) case 8 * LL + VV: wtwiddles<LL, VV>(out); return true;
+#define PSTD_WCASE_PERSIST(LL, VV) case 8 * LL + VV: return wlaunch_persist<LL, VV>(g, st, a);
+#define PSTD_WCASE_PBLOCKS(LL, VV) case 8 * LL + VV: return wpersist_blocks<LL, VV>(threads, smem, blocks);
 
 // Lanes per sequence of Sched<L, 2> (fewer, wider passes; 0: none).
 inline int wlanes_v2(int L) { return L == 1024 ? 64 : 0; }
+// Lanes per sequence of Sched<L, 4> (the latency radices, tables in shared
+// memory; 0: none).
+inline int wlanes_v4(int L) { return L == 512 ? 64 : (L == 256 ? 32 : 0); }
 // Lanes per sequence of Sched<L, 3> (more lanes, 4 elements each; 0: none).
 inline int wlanes_v3(int L) { return L == 1024 ? 256 : (L == 512 ? 128 : 0); }
 

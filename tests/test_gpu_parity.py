@@ -100,6 +100,41 @@ def test_one_step_matches_oracle(ncells, bcs):
     s.close()
 
 
+@pytest.mark.parametrize("sched", [
+    [(0, 1), (0, 1)], [(1, 1), (1, 2)], [(1, 2), (1, 4)], [(4, 1), (4, 1)], [(4, 2), (4, 4)],
+    [(4, 4), (3, 1)], [(1, 4), (4, 2)],
+])
+def test_every_schedule_matches_oracle(sched):
+    """Every register-FFT schedule an axis can take (variant x line pairs per
+    CTA) gives the oracle's step: FFT lengths 256 (axis 0) and 512 (axis 1),
+    strided tiles with a ragged, odd inner extent (axis 1: 27 lines apart) and
+    the phantom partner of the unpaired line."""
+    from paper_2005_00322_gb300 import Solver
+    ncells, bcs = (128, 256, 27), [("D", "D"), ("N", "N"), ("N", "D")]
+    dt = pstd.dt_from_cfl(0.25 / np.sqrt(3), DX, 1500.0)
+    s = Solver(ncells, DX, bcs, dt=dt, schedule=sched)
+    assert [sc[0] for sc in s.schedule()[:2]] == [v for v, _ in sched]
+    assert [sc[2] for sc in s.schedule()[:2]] == [q for _, q in sched]
+    od = pstd.Desc(ncells, (DX,), bcs, dt=dt)
+    p0 = inputs.random_field(s.shapes[0], 11).astype(np.float32).astype(np.float64)
+    u0 = [inputs.random_field(sh, 12 + i).astype(np.float32).astype(np.float64) * 1e-6
+          for i, sh in enumerate(s.shapes[1:])]
+    p, us = dev(p0), [dev(u) for u in u0]
+    s.step(p, us)
+    ref = pstd.step(od, pstd.State(p0, u0))
+    assert rel_l2(host(p), ref.p) < 1e-5
+    for i in range(3):
+        assert rel_l2(host(us[i]), ref.u[i]) < 1e-5
+    s.close()
+
+
+def test_unavailable_variant_is_rejected():
+    from paper_2005_00322_gb300 import Solver
+    from paper_2005_00322_gb300._abi import PstdError
+    with pytest.raises(PstdError, match="EINVAL"):
+        Solver((96, 64), DX, [("N", "N"), ("D", "D")], cfl=0.2, schedule=[(4, 1), None])   # L = 192
+
+
 @pytest.mark.parametrize("ncells,bcs", CASES[:8])
 @pytest.mark.parametrize("uinit", ["halfstep", "as_given"])
 def test_short_run_matches_oracle(ncells, bcs, uinit):
