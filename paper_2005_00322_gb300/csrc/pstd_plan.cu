@@ -383,9 +383,51 @@ void gemm_fragments(const std::vector<double>& D, int M, int K, std::vector<uint
             }
 }
 
-// In-place radix-2 FFT of a power-of-two length (FP64, host): forward
-// X_k = sum_j x_j e^{-2 pi i j k / n}.
+void host_fft_pow2(std::vector<std::complex<double>>& x);
+
+// Forward DFT X_k = sum_j x_j e^{-2 pi i j k / n} (FP64, host) of any length:
+// radix 2 for powers of two, otherwise decimation in time over the smallest
+// prime factor p (p interleaved sub-transforms of length n / p, combined with
+// the twiddles e^{-2 pi i r k / n}), down to direct sums at prime lengths.
 void host_fft(std::vector<std::complex<double>>& x) {
+    const size_t n = x.size();
+    if (n <= 1) return;
+    if ((n & (n - 1)) == 0) {
+        host_fft_pow2(x);
+        return;
+    }
+    size_t p = 2;
+    while (n % p) ++p;
+    auto unit = [n](size_t e) {   // e^{-2 pi i e / n}, e reduced mod n
+        const double ang = -2.0 * M_PI * (double)(e % n) / (double)n;
+        return std::complex<double>(std::cos(ang), std::sin(ang));
+    };
+    std::vector<std::complex<double>> y(n);
+    if (p == n) {
+        for (size_t k = 0; k < n; ++k) {
+            std::complex<double> acc = 0;
+            for (size_t j = 0; j < n; ++j) acc += x[j] * unit(j * k);
+            y[k] = acc;
+        }
+        x.swap(y);
+        return;
+    }
+    const size_t m = n / p;
+    std::vector<std::vector<std::complex<double>>> sub(p, std::vector<std::complex<double>>(m));
+    for (size_t r = 0; r < p; ++r) {
+        for (size_t j = 0; j < m; ++j) sub[r][j] = x[j * p + r];
+        host_fft(sub[r]);
+    }
+    for (size_t k = 0; k < n; ++k) {
+        std::complex<double> acc = 0;
+        for (size_t r = 0; r < p; ++r) acc += sub[r][k % m] * unit(r * k);
+        y[k] = acc;
+    }
+    x.swap(y);
+}
+
+// In-place radix-2 FFT of a power-of-two length (FP64, host), same sign.
+void host_fft_pow2(std::vector<std::complex<double>>& x) {
     const size_t n = x.size();
     for (size_t i = 1, j = 0; i < n; ++i) {
         size_t bit = n >> 1;
@@ -674,9 +716,24 @@ int build_axis(pstd_plan_s* P, int i) {
     const bool fft_ok = radix_schedule(a.L, a.fft);
     a.kind = fft_ok ? 0 : (a.N <= kDenseMaxN ? 1 : 2);
     if (a.kind == 2) {
-        int M2 = 1;
-        while (M2 < 2 * a.L - 1) M2 *= 2;
-        if (M2 > kConvMaxFft || !radix_schedule(M2, a.fft)) return PSTD_EUNSUPPORTED;
+        // The linear convolution needs a circular length M2 >= 2L - 1.  Of the
+        // lengths with an FFT schedule (2^a 3^b 5^c) up to the next power of
+        // two, take the one with the least shared-memory traffic in the
+        // Stockham passes, M2 x passes (the power of two on a tie).
+        int pow2 = 1;
+        while (pow2 < 2 * a.L - 1) pow2 *= 2;
+        int M2 = 0;
+        int64_t best = 0;
+        pstd::FftPlan cand{};
+        for (int m = pow2; m >= 2 * a.L - 1; --m) {
+            if (m > kConvMaxFft || !radix_schedule(m, cand)) continue;
+            const int64_t cost = (int64_t)m * cand.npass;
+            if (M2 == 0 || cost < best) {
+                M2 = m;
+                best = cost;
+            }
+        }
+        if (M2 == 0 || !radix_schedule(M2, a.fft)) return PSTD_EUNSUPPORTED;
         a.M2 = M2;
     }
 
