@@ -129,7 +129,9 @@ int pstd_plan(const pstd_desc* desc, void* stream, pstd_plan_t** out);
  * default for those lengths on axes with too few lines to fill the GPU),
  * variant 4 (lengths 256, 512) variant 1's FFT with its coefficient and
  * twiddle tables read from shared memory instead of registers (fewer
- * registers per thread, more resident CTAs).  An unavailable variant gives
+ * registers per thread, more resident CTAs), variant 5 (lengths 256, 512)
+ * the same with the tables read from global memory through L1 (neither
+ * registers nor shared memory hold them).  An unavailable variant gives
  * PSTD_EINVAL.
  * seqs_per_cta: line pairs per CTA (a power of two). */
 typedef struct {

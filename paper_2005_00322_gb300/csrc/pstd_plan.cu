@@ -832,7 +832,11 @@ int build_axis(pstd_plan_s* P, int i) {
     int V = 0;
     int os = P->opts.seqs_per_cta[i];
     const int ov = P->opts.variant[i];
-    if (ov == 4) {
+    if (ov == 5) {
+        if (pstd::wlanes_v5(a.L) == 0) return PSTD_EINVAL;
+        V = 5;
+        T = pstd::wlanes_v5(a.L);
+    } else if (ov == 4) {
         if (pstd::wlanes_v4(a.L) == 0) return PSTD_EINVAL;
         V = 4;
         T = pstd::wlanes_v4(a.L);
@@ -873,7 +877,7 @@ int build_axis(pstd_plan_s* P, int i) {
     // run 8 words (one 32-byte sector); measured 0.815 -> 0.768 ms per 256^3
     // step.  The shared-table schedule takes 4 on contiguous axes too.  Not
     // for the persistent run, whose axes share one CTA size.
-    if (auto_os && os == 2 && !P->opts.persistent && (inner > 1 || V == 4) && T <= 64 &&
+    if (auto_os && os == 2 && !P->opts.persistent && (inner > 1 || V >= 4) && T <= 64 &&
         (a.nlines + 1) / 2 >= 4 * 2 * nsm)
         os = 4;
     if (a.kind == 0 && T > 0) {
@@ -950,7 +954,7 @@ int build_axis(pstd_plan_s* P, int i) {
             a.wgeo.grid = (unsigned)((nseq + w.seqs - 1) / w.seqs);
             a.wgeo.smem = (size_t)w.seqs * pstd::wseq_words(a.L) * sizeof(float2);
             a.wgeo.smem += pstd::wk::contig_stage_floats(w) * sizeof(float);  // staged slots and accumulator
-            a.wgeo.smem += (wt.size() + 4 * (size_t)a.L) * sizeof(float2);   // staged tables
+            if (V != 5) a.wgeo.smem += (wt.size() + 4 * (size_t)a.L) * sizeof(float2);   // staged tables
         } else {
             const int64_t outer = a.nlines / a.inner;
             auto tiles = [&](int th) {
@@ -962,7 +966,7 @@ int build_axis(pstd_plan_s* P, int i) {
             w.G = 2 * w.seqs;
             a.wgeo.grid = (unsigned)tiles(threads);
             a.wgeo.smem = pstd::wk::strided_step_floats(w, pstd::wseq_words(a.L), true) * sizeof(float);
-            a.wgeo.smem += (wt.size() + 4 * (size_t)a.L) * sizeof(float2);   // staged tables
+            if (V != 5) a.wgeo.smem += (wt.size() + 4 * (size_t)a.L) * sizeof(float2);   // staged tables
         }
         a.wgeo.threads = threads;
         if (a.wgeo.smem > 200 * 1024) return PSTD_EUNSUPPORTED;

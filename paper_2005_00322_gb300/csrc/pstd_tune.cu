@@ -123,9 +123,9 @@ extern "C" int pstd_plan_autotune(const pstd_desc* desc, void* stream, const pst
     for (int a = 0; a < desc->ndim && rc == PSTD_OK; ++a) {
         const int L = fft_length(desc, a);
         if (L <= 0 || pstd::wlanes(L) == 0) continue;
-        const int lanes[5] = {pstd::wlanes(L), pstd::wlanes_latency(L), pstd::wlanes_v2(L), pstd::wlanes_v3(L),
-                              pstd::wlanes_v4(L)};
-        for (int v = 0; v < 5; ++v) {
+        const int lanes[6] = {pstd::wlanes(L), pstd::wlanes_latency(L), pstd::wlanes_v2(L), pstd::wlanes_v3(L),
+                              pstd::wlanes_v4(L), pstd::wlanes_v5(L)};
+        for (int v = 0; v < 6; ++v) {
             if (lanes[v] == 0) continue;
             for (int sq = 1; sq * lanes[v] <= 256; sq *= 2) {
                 if (sq * lanes[v] < 32) continue;

@@ -264,11 +264,16 @@ PSTD_HD void derivative(float2 (&v)[S::E], int t, float2* sm, const WAxis& A, co
 }
 
 // Schedules whose lanes hold at most 8 elements keep their tables in
-// registers (except V = 4, which trades them for occupancy); the others
-// stage them in shared memory.
+// registers (except V = 4 and 5, which trade them for occupancy); the others
+// stage them in shared memory, except V = 5, which reads them from global
+// memory (L1-cached) where they are.
 template <class S>
 constexpr bool reg_tables() {
-    return S::V >= 1 && S::V != 4 && S::E <= 8;
+    return S::V >= 1 && S::V != 4 && S::V != 5 && S::E <= 8;
+}
+template <class S>
+constexpr bool staged_tables() {
+    return !reg_tables<S>() && S::V != 5;
 }
 
 // Tables of one derivative for schedule S (registers for the latency
@@ -304,7 +309,7 @@ PSTD_HD void lane_of(int tid, int& seq, int& t) {
 template <class S>
 PSTD_HD float2* stage_tables(WAxis& A, const float2*& f1, const float2*& f2, float2* dst, int tid,
                              int nthr) {
-    if constexpr (reg_tables<S>()) return dst;   // these schedules keep tables in registers
+    if constexpr (!staged_tables<S>()) return dst;   // tables in registers or read in place
     constexpr int ntw = (wf::tw_total<S>() + 1) & ~1;
     constexpr int L = S::L;
     float2* p = dst;

@@ -118,7 +118,9 @@ struct Dft {
 // lines.  V = 1 (latency): 8 elements per lane spread over up to 128 lanes,
 // for axes with too few lines to fill the GPU, where one sequence's latency
 // sets the pass time.  V = 4: the radices of V = 1 with the tables read from
-// shared memory instead of registers (fewer registers, more resident CTAs).  A sequence wider than a warp exchanges through a CTA
+// shared memory instead of registers (fewer registers, more resident CTAs).
+// V = 5: the same with the tables read from global memory through L1, so
+// that neither registers nor shared memory hold them.  A sequence wider than a warp exchanges through a CTA
 // barrier.
 template <int L, int V = 0>
 struct Sched;
@@ -152,6 +154,8 @@ PSTD_SCHED(1024, 3, 256, 4, 4, 4, 4, 4)
 PSTD_SCHED(512, 3, 128, 4, 4, 4, 4, 2)
 PSTD_SCHED(256, 4, 32, 8, 8, 4)
 PSTD_SCHED(512, 4, 64, 8, 8, 8)
+PSTD_SCHED(256, 5, 32, 8, 8, 4)
+PSTD_SCHED(512, 5, 64, 8, 8, 8)
 #undef PSTD_SCHED
 
 // Ns before pass p (product of earlier radices)

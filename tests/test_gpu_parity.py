@@ -102,7 +102,7 @@ def test_one_step_matches_oracle(ncells, bcs):
 
 @pytest.mark.parametrize("sched", [
     [(0, 2), (0, 4)], [(1, 1), (1, 2)], [(1, 2), (1, 4)], [(4, 1), (4, 1)], [(4, 2), (4, 4)],
-    [(4, 4), (3, 1)], [(1, 4), (4, 2)],
+    [(4, 4), (3, 1)], [(1, 4), (4, 2)], [(5, 1), (5, 2)], [(5, 4), (5, 4)], [(4, 2), (5, 1)],
 ])
 def test_every_schedule_matches_oracle(sched):
     """Every register-FFT schedule an axis can take (variant x line pairs per
