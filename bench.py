@@ -346,7 +346,7 @@ class SingleRunner:
 class BatchRunner:
     """Independent grids in one batch (pstd_batch_*): wall combinations or a batch."""
 
-    def __init__(self, w):
+    def __init__(self, w, persistent=False):
         import torch
         from paper_2005_00322_gb300.batch import Batch, reflection_combos
         self.w = w
@@ -363,6 +363,9 @@ class BatchRunner:
             p_full = [full] * len(specs)
             self.steps = w.steps
         self.batch = Batch(specs)
+        if persistent:
+            # every run as one cooperative kernel over all members
+            self.batch.set_persistent()
         self.stream = self.batch.stream
         self.fields = self.batch.zeros()
         self.p0 = []
@@ -542,7 +545,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the plan's default axis-pass schedules (no pstd_plan_autotune)")
     ap.add_argument("--persistent", action="store_true",
-                    help="pstd_run as one cooperative kernel with grid barriers")
+                    help="pstd_run (a batch: pstd_batch_run over all members) as one cooperative kernel "
+                         "with grid barriers")
     ap.add_argument("--form", default="fft", choices=["fft", "split", "split-bf16", "tensor", "order2"],
                     help="fft: spectral FFT route; split: FP16 hi/lo dense form (mma.sync); split-bf16: "
                          "BF16 three-way split dense form on tcgen05; tensor: TF32 hi/lo dense form on "
@@ -579,7 +583,8 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
 
-    run = SingleRunner(w, args.form, args.persistent, not args.no_autotune) if single else BatchRunner(w)
+    run = (SingleRunner(w, args.form, args.persistent, not args.no_autotune) if single
+           else BatchRunner(w, args.persistent))
     st = run.stream
     steps_per = members_of(w)[0].steps
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2

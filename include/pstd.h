@@ -371,6 +371,34 @@ int pstd_batch_free(pstd_batch_t* batch);
 /* Kernels launched by the last batch call (graph replays count their nodes). */
 int64_t pstd_batch_last_launch_count(const pstd_batch_t* batch);
 
+/* Run every later pstd_batch_run (enable != 0) as ONE cooperative kernel over
+ * all members (Section 5's independent runs computed together): each step's
+ * axis passes, last axis first, are split into work items (line groups or
+ * tiles) over all members, which the resident CTAs take in turn, meeting at a
+ * software grid barrier between passes.  When every axis of every member has
+ * the same register-FFT schedule (e.g. the 4^d wall combinations of one
+ * grid) the kernel runs those passes, with each member's velocity conversion
+ * before and after it; otherwise every axis runs the generic shared-memory
+ * program (its own FFT, convolution or dense route).  Each barrier wait is
+ * bounded by spin_limit polls (0: a default of about a second); on giving up
+ * the kernel ends and pstd_batch_sync reports PSTD_ETIMEOUT.
+ * withhold_arrivals > 0 makes every barrier wait for that many arrivals that
+ * never come (to test the bounded wait).  Results equal the graph path's bit
+ * for bit on the register-FFT kernel and on members whose axes all take the
+ * generic program there too; a register-FFT axis run by the generic program
+ * agrees to rounding.  Errors: PSTD_EINVAL; PSTD_EUNSUPPORTED for a
+ * dense-operator form (pstd_plan_opts.form != 0 is not set by pstd_batch_plan,
+ * so this does not arise for its members). */
+int pstd_batch_set_persistent(pstd_batch_t* batch, int enable, long long spin_limit, int withhold_arrivals);
+
+/* The cooperative kernel pstd_batch_set_persistent would use: 1 register-FFT
+ * passes, 2 the generic program.  Errors: PSTD_EINVAL. */
+int pstd_batch_persistent_kind(const pstd_batch_t* batch);
+
+/* Wait for the batch's stream.  PSTD_ETIMEOUT (reported once) if a barrier
+ * wait of the last cooperative run gave up.  Errors: PSTD_ECUDA. */
+int pstd_batch_sync(pstd_batch_t* batch);
+
 /* Section 5 on the host: for per-axis reflection coefficients
  * refl[2 i] = R_L, refl[2 i + 1] = R_R, write the 4^ndim wall combinations as
  * copies of *tmpl with bc replaced (axis 0 slowest; per axis in the order

@@ -50,6 +50,9 @@ SIGNATURES = {
     "pstd_batch_combine": (c_int, [c_void_p, POINTER(c_double), POINTER(c_void_p), c_void_p]),
     "pstd_batch_free": (c_int, [c_void_p]),
     "pstd_batch_last_launch_count": (c_int64, [c_void_p]),
+    "pstd_batch_set_persistent": (c_int, [c_void_p, c_int, ctypes.c_longlong, c_int]),
+    "pstd_batch_persistent_kind": (c_int, [c_void_p]),
+    "pstd_batch_sync": (c_int, [c_void_p]),
     "pstd_reflection_combos": (c_int, [c_void_p, POINTER(c_double), c_void_p, POINTER(c_double)]),
     "pstd_step_noalloc": (c_int, [c_void_p, c_void_p, POINTER(c_void_p), c_int64, c_void_p]),
     "pstd_nn_gemm": (c_int, [c_void_p, c_void_p]),

@@ -136,6 +136,21 @@ class Batch:
     def last_launch_count(self) -> int:
         return int(self.lib.pstd_batch_last_launch_count(self._h))
 
+    def set_persistent(self, enable=True, spin_limit=0, withhold_arrivals=0):
+        """Later runs as one cooperative kernel over all members (pstd_batch_set_persistent)."""
+        _abi.check(self.lib, self.lib.pstd_batch_set_persistent(self._h, 1 if enable else 0, int(spin_limit),
+                                                                int(withhold_arrivals)),
+                   "pstd_batch_set_persistent")
+
+    def persistent_kind(self) -> str:
+        """Which cooperative kernel a persistent run uses: "register" or "generic"."""
+        k = self.lib.pstd_batch_persistent_kind(self._h)
+        return {1: "register", 2: "generic"}.get(k, "none")
+
+    def sync(self):
+        """Wait for the batch; raises PstdError (PSTD_ETIMEOUT) if a barrier wait gave up."""
+        _abi.check(self.lib, self.lib.pstd_batch_sync(self._h), "pstd_batch_sync")
+
     def close(self):
         if getattr(self, "_h", None):
             self.lib.pstd_batch_free(self._h)

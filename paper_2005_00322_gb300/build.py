@@ -23,11 +23,11 @@ LIB = os.path.join(LIBDIR, "libpstd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]
-# The register-FFT pass units write every multiply-add of the pass explicitly
-# (rfma in pstd_ops.cuh); with contraction off, no other product is fused, so
-# the per-axis kernels and the cooperative kernel, which inline the same pass
-# code, round identically.
-NO_CONTRACT = ("pstd_wkernels_",)
+# The pass units (register-FFT and generic) write every multiply-add of a
+# pass explicitly (rfma in pstd_ops.cuh); with contraction off, no other
+# product is fused, so the per-axis kernels and the cooperative kernels,
+# which inline the same pass code, round identically.
+NO_CONTRACT = ("pstd_wkernels_", "pstd_kernels")
 
 
 def nvcc() -> str:

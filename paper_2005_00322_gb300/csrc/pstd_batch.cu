@@ -73,6 +73,11 @@ struct pstd_batch_s {
     cudaGraphExec_t exec = nullptr;
     int64_t graph_launches = 0;
     int64_t last_launches = 0;
+    // one cooperative kernel per run (pstd_batch_set_persistent)
+    int persistent = 0;
+    long long spin_limit = 0;
+    unsigned withhold = 0;
+    pstd_batch_persist_s* ps = nullptr;
 };
 
 namespace {
@@ -84,6 +89,7 @@ namespace {
     } while (0)
 
 void batch_release(pstd_batch_s* B) {
+    pstd_internal_batch_persist_free(B->ps);
     if (B->exec) cudaGraphExecDestroy(B->exec);
     for (auto* p : B->plans) pstd_free(p);
     for (auto s : B->streams) cudaStreamDestroy(s);
@@ -197,6 +203,18 @@ int pstd_batch_run(pstd_batch_t* B, float* const* p, float* const* u, int64_t ns
     B->last_launches = 0;
     if (nsteps == 0) return PSTD_OK;
     int64_t conv = 0;
+    if (B->persistent) {
+        // every member's steps in one cooperative kernel on the batch stream;
+        // the register-FFT kernel works on the velocities' spectrum form
+        const int kind = pstd_internal_batch_persist_kind(B->plans.data(), B->n);
+        int rc = kind == 1 ? convert_block(B, u, 1, &conv) : PSTD_OK;
+        if (rc == PSTD_OK)
+            rc = pstd_internal_batch_persist_run(&B->ps, B->plans.data(), B->n, p, u, nsteps, B->spin_limit,
+                                                 B->withhold, B->stream);
+        if (rc == PSTD_OK && kind == 1) rc = convert_block(B, u, 0, &conv);
+        B->last_launches = conv + 1;
+        return rc;
+    }
     int rc = convert_block(B, u, 1, &conv);
     if (rc == PSTD_OK) rc = batch_steps(B, p, u, nsteps);
     if (rc == PSTD_OK) rc = convert_block(B, u, 0, &conv);
@@ -286,6 +304,27 @@ int pstd_batch_free(pstd_batch_t* B) {
 }
 
 int64_t pstd_batch_last_launch_count(const pstd_batch_t* B) { return B ? B->last_launches : 0; }
+
+int pstd_batch_set_persistent(pstd_batch_t* B, int enable, long long spin_limit, int withhold_arrivals) {
+    if (!B || spin_limit < 0 || withhold_arrivals < 0) return PSTD_EINVAL;
+    if (enable && pstd_internal_batch_persist_kind(B->plans.data(), B->n) == 0) return PSTD_EUNSUPPORTED;
+    B->persistent = enable ? 1 : 0;
+    B->spin_limit = spin_limit;
+    B->withhold = (unsigned)withhold_arrivals;
+    return PSTD_OK;
+}
+
+int pstd_batch_persistent_kind(const pstd_batch_t* B) {
+    if (!B) return PSTD_EINVAL;
+    return pstd_internal_batch_persist_kind(B->plans.data(), B->n);
+}
+
+int pstd_batch_sync(pstd_batch_t* B) {
+    if (!B) return PSTD_EINVAL;
+    BCK(cudaStreamSynchronize(B->stream));
+    BCK(cudaGetLastError());
+    return pstd_internal_batch_persist_status(B->ps);
+}
 
 int pstd_reflection_combos(const pstd_desc* tmpl, const double* refl, pstd_desc* descs, double* w) {
     if (!tmpl || !refl || !descs || !w || tmpl->ndim < 1 || tmpl->ndim > 3) return PSTD_EINVAL;

@@ -56,6 +56,18 @@ struct GradArgs {
                             // here (may be `in`: each entry belongs to one line)
 };
 
+// A batch of plans run as one cooperative kernel on the generic CTA program:
+// pass k of a step (k = 0 the last axis of each member) is, over all members,
+// prefix[k][members] work items (line groups), member m owning items
+// prefix[k][m] .. prefix[k][m + 1] - 1 with its pass mem[m * 3 + k].
+struct StepPersistArgs {
+    const StepArgs* mem;       // [members][3], device memory
+    const int64_t* prefix;     // [3][members + 1], device memory
+    int members;
+    int npass;                 // passes per step: the most axes of any member
+    int64_t nsteps;
+};
+
 PSTD_HD int64_t line_base(int64_t l, int64_t inner, int len) {
     return (l / inner) * (int64_t)len * inner + (l % inner);
 }

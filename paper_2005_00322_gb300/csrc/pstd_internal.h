@@ -22,3 +22,24 @@ cudaStream_t pstd_internal_stream(const pstd_plan_t* P);
 void pstd_internal_layout(const pstd_plan_t* P, int lo[3], int64_t shape[3]);
 // Record a CUDA error text for pstd_last_cuda_error().
 int pstd_internal_cuda_fail(cudaError_t e, const char* what);
+
+// A batch of plans as one cooperative kernel per run (pstd_batch_set_persistent).
+struct pstd_batch_persist_s;
+// Which cooperative kernel the plans allow: 1 the register-FFT passes (every
+// axis of every member on one register schedule; the velocities are in their
+// spectrum form around the run, as for pstd_internal_launch_steps), 2 the
+// generic CTA program on every axis (velocities as stored), 0 none (a
+// dense-operator form).
+int pstd_internal_batch_persist_kind(pstd_plan_t* const* plans, int n);
+// Launch `nsteps` steps of every member (fields p[m], u[3 m + a]) as one
+// cooperative kernel on stream st; *state (created on first use) holds the
+// device copies of the passes and the grid barrier.  spin_limit: polls before
+// a wait gives up (0: default); withhold: extra arrivals the barrier waits
+// for (tests of the bounded wait).
+int pstd_internal_batch_persist_run(pstd_batch_persist_s** state, pstd_plan_t* const* plans, int n, float* const* p,
+                                    float* const* u, int64_t nsteps, long long spin_limit, unsigned withhold,
+                                    cudaStream_t st);
+// PSTD_ETIMEOUT once if a wait of the last cooperative run gave up (the
+// caller has synchronised), else PSTD_OK.
+int pstd_internal_batch_persist_status(pstd_batch_persist_s* state);
+void pstd_internal_batch_persist_free(pstd_batch_persist_s* state);

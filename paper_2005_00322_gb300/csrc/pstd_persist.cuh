@@ -12,80 +12,48 @@
 // context usable.
 #pragma once
 
+#include "pstd_gridsync.cuh"
 #include "pstd_wcta.cuh"
 
 namespace pstd {
 
-struct GridSync {
-    unsigned* count;         // arrivals at the current barrier
-    unsigned* gen;           // barrier generation
-    int* status;             // 0 ok, 1 a wait gave up
-    unsigned expected;       // arrivals that release a barrier (gridDim.x, more to test a stall)
-    long long spin_limit;    // polls before giving up
-};
-
+// One plan (members == 0: the passes in ax / strided / items) or a batch of
+// plans on one schedule (members > 0): pass k of a step (k = 0 the last axis)
+// is, over all members, prefix[k][members] work items, member m owning items
+// prefix[k][m] .. prefix[k][m + 1] - 1 with its pass mem[m * 3 + k].
 struct PersistArgs {
     WStep ax[3];
     int strided[3];
     int64_t items[3];        // work items of each axis pass
-    int ndim;
+    int ndim;                // axis passes per step (a batch: the most of any member)
     int64_t nsteps;
     GridSync sync;
+    int members;
+    const WStep* mem;        // [members][3], device memory
+    const int64_t* prefix;   // [3][members + 1], device memory
 };
-
-#ifdef __CUDA_ARCH__
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ int ld_acquire_i(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Barrier of all CTAs of the launch; false if a bounded wait gave up (here or
-// in another CTA).  All threads of every CTA must call it.
-__device__ bool grid_sync(const GridSync& g) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ok = 1;
-        const unsigned my_gen = ld_acquire(g.gen);
-        __threadfence();
-        const unsigned arrived = atomicAdd(g.count, 1u) + 1u;
-        if (arrived == g.expected) {
-            atomicExch(g.count, 0u);
-            __threadfence();
-            atomicAdd(g.gen, 1u);
-        } else {
-            long long spins = 0;
-            while (ld_acquire(g.gen) == my_gen) {
-                if (ld_acquire_i(g.status) != 0 || ++spins > g.spin_limit) {
-                    atomicExch(g.status, 1);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return ok != 0;
-}
-#endif
 
 template <class S>
 __device__ void persistent_run(const PersistArgs& a, float2* smem) {
 #ifdef __CUDA_ARCH__
     for (int64_t s = 0; s < a.nsteps; ++s) {
-        for (int ax = a.ndim - 1; ax >= 0; --ax) {
-            for (int64_t it = blockIdx.x; it < a.items[ax]; it += gridDim.x) {
-                if (a.strided[ax]) wk::step_strided<S>(a.ax[ax], it, smem, threadIdx.x, blockDim.x);
-                else wk::step_contig<S>(a.ax[ax], it, smem, threadIdx.x, blockDim.x);
-                __syncthreads();     // shared memory is reused by the next item
+        for (int k = 0; k < a.ndim; ++k) {
+            if (a.members == 0) {
+                const int ax = a.ndim - 1 - k;
+                for (int64_t it = blockIdx.x; it < a.items[ax]; it += gridDim.x) {
+                    if (a.strided[ax]) wk::step_strided<S>(a.ax[ax], it, smem, threadIdx.x, blockDim.x);
+                    else wk::step_contig<S>(a.ax[ax], it, smem, threadIdx.x, blockDim.x);
+                    __syncthreads();     // shared memory is reused by the next item
+                }
+            } else {
+                const int64_t* pre = a.prefix + (size_t)k * (a.members + 1);
+                for (int64_t it = blockIdx.x; it < pre[a.members]; it += gridDim.x) {
+                    const int m = member_of(pre, a.members, it);
+                    const WStep& w = a.mem[(size_t)m * 3 + k];
+                    if (w.ax.inner > 1) wk::step_strided<S>(w, it - pre[m], smem, threadIdx.x, blockDim.x);
+                    else wk::step_contig<S>(w, it - pre[m], smem, threadIdx.x, blockDim.x);
+                    __syncthreads();
+                }
             }
             if (!grid_sync(a.sync)) return;
         }

@@ -36,6 +36,9 @@ namespace pstd {
 cudaError_t launch_k_step(unsigned grid, size_t smem, cudaStream_t st, const StepArgs& a);
 cudaError_t launch_k_grad(unsigned grid, size_t smem, cudaStream_t st, const GradArgs& a);
 cudaError_t set_max_smem(int bytes);
+cudaError_t launch_k_step_persist(unsigned grid, size_t smem, cudaStream_t st, const StepPersistArgs& a,
+                                  const GridSync& sync);
+cudaError_t k_step_persist_blocks(size_t smem, int* blocks);
 cudaError_t launch_k_axpby(int64_t n, float alpha, const float* x, float beta, float* y, cudaStream_t st);
 // register-FFT passes, one dispatcher per translation unit (pstd_wkernels_*.cu)
 cudaError_t wsmall_step(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WStep& a);
@@ -67,6 +70,8 @@ using pstd::WGrad;
 using pstd::WLaunch;
 using pstd::WStep;
 using pstd::PersistArgs;
+using pstd::GridSync;
+using pstd::StepPersistArgs;
 
 namespace {
 
@@ -1478,6 +1483,163 @@ int pstd_internal_launch_steps(pstd_plan_t* P, float* p, float* const* u, int64_
     for (int64_t s = 0; s < n; ++s) {
         int rc = launch_step(P, p, u, launches);
         if (rc != PSTD_OK) return rc;
+    }
+    return PSTD_OK;
+}
+
+// ---- batch of plans as one cooperative kernel ------------------------------
+struct pstd_batch_persist_s {
+    std::vector<unsigned char> h_args;   // WStep or StepArgs, [members][3]
+    std::vector<int64_t> h_prefix;       // [3][members + 1]
+    void* d_args = nullptr;
+    int64_t* d_prefix = nullptr;
+    size_t args_cap = 0, prefix_cap = 0;
+    unsigned* d_sync = nullptr;          // count, generation, status
+};
+
+int pstd_internal_batch_persist_kind(pstd_plan_t* const* plans, int n) {
+    if (n < 1) return 0;
+    for (int m = 0; m < n; ++m)
+        if (plans[m]->opts.form != 0) return 0;
+    const Axis& A0 = plans[0]->ax[0];
+    bool reg = true;
+    for (int m = 0; m < n && reg; ++m)
+        for (int a = 0; a < plans[m]->ndim && reg; ++a) {
+            const Axis& A = plans[m]->ax[a];
+            reg = A.wl > 0 && A0.wl > 0 && A.L == A0.L && A.wv == A0.wv && A.wgeo.threads == A0.wgeo.threads;
+        }
+    return reg ? 1 : 2;
+}
+
+void pstd_internal_batch_persist_free(pstd_batch_persist_s* S) {
+    if (!S) return;
+    if (S->d_args) cudaFree(S->d_args);
+    if (S->d_prefix) cudaFree(S->d_prefix);
+    if (S->d_sync) cudaFree(S->d_sync);
+    delete S;
+}
+
+int pstd_internal_batch_persist_status(pstd_batch_persist_s* S) {
+    if (!S || !S->d_sync) return PSTD_OK;
+    int status = 0;
+    CK(cudaMemcpy(&status, S->d_sync + 2, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status != 0) {
+        CK(cudaMemset(S->d_sync, 0, 4 * sizeof(unsigned)));
+        return PSTD_ETIMEOUT;
+    }
+    return PSTD_OK;
+}
+
+int pstd_internal_batch_persist_run(pstd_batch_persist_s** state, pstd_plan_t* const* plans, int n, float* const* p,
+                                    float* const* u, int64_t nsteps, long long spin_limit, unsigned withhold,
+                                    cudaStream_t st) {
+    const int kind = pstd_internal_batch_persist_kind(plans, n);
+    if (kind == 0) return PSTD_EUNSUPPORTED;
+    if (!*state) {
+        *state = new (std::nothrow) pstd_batch_persist_s();
+        if (!*state) return PSTD_ENOMEM;
+        CK(cudaMalloc((void**)&(*state)->d_sync, 4 * sizeof(unsigned)));
+        CK(cudaMemset((*state)->d_sync, 0, 4 * sizeof(unsigned)));
+    }
+    pstd_batch_persist_s* S = *state;
+    int npass = 0;
+    for (int m = 0; m < n; ++m) npass = plans[m]->ndim > npass ? plans[m]->ndim : npass;
+    const size_t esz = kind == 1 ? sizeof(WStep) : sizeof(StepArgs);
+    S->h_args.assign((size_t)n * 3 * esz, 0);
+    S->h_prefix.assign((size_t)3 * (n + 1), 0);
+    size_t smem = 0;
+    int64_t most = 0;
+    for (int k = 0; k < npass; ++k) {
+        int64_t* pre = S->h_prefix.data() + (size_t)k * (n + 1);
+        for (int m = 0; m < n; ++m) {
+            pstd_plan_s* P = plans[m];
+            int64_t items = 0;
+            const int a = P->ndim - 1 - k;
+            if (a >= 0) {
+                Axis& A = P->ax[a];
+                unsigned char* slot = S->h_args.data() + ((size_t)m * 3 + k) * esz;
+                if (kind == 1) {
+                    WStep w;
+                    w.ax = A.wax;
+                    w.fP = A.d_f[OP_STEP_P];
+                    w.fU = A.d_fUL;
+                    w.p = p[m];
+                    w.u = u[3 * m + a];
+                    w.acc_in = (a == P->ndim - 1) ? p[m] : P->d_S;
+                    w.acc_out = (a == 0) ? p[m] : P->d_S;
+                    std::memcpy(slot, &w, sizeof w);
+                    items = A.wgeo.grid;
+                    smem = A.wgeo.smem > smem ? A.wgeo.smem : smem;
+                } else {
+                    const StepArgs sa = step_args(P, a, p[m], u + 3 * m);
+                    std::memcpy(slot, &sa, sizeof sa);
+                    items = (A.nlines + A.G - 1) / A.G;
+                    smem = A.smem > smem ? A.smem : smem;
+                }
+            }
+            pre[m + 1] = pre[m] + items;
+        }
+        most = pre[n] > most ? pre[n] : most;
+    }
+    if (S->h_args.size() > S->args_cap) {
+        if (S->d_args) cudaFree(S->d_args);
+        S->d_args = nullptr;
+        S->args_cap = 0;
+        CK(cudaMalloc(&S->d_args, S->h_args.size()));
+        S->args_cap = S->h_args.size();
+    }
+    if (S->h_prefix.size() > S->prefix_cap) {
+        if (S->d_prefix) cudaFree(S->d_prefix);
+        S->d_prefix = nullptr;
+        S->prefix_cap = 0;
+        CK(cudaMalloc((void**)&S->d_prefix, S->h_prefix.size() * sizeof(int64_t)));
+        S->prefix_cap = S->h_prefix.size();
+    }
+    // pageable sources: each copy has consumed its source when the call returns
+    CK(cudaMemcpyAsync(S->d_args, S->h_args.data(), S->h_args.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(S->d_prefix, S->h_prefix.data(), S->h_prefix.size() * sizeof(int64_t),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(S->d_sync, 0, sizeof(unsigned), st));   // arrival count
+    int dev = 0, nsm = 0, per_sm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const Axis& A0 = plans[0]->ax[0];
+    if (kind == 1) CK(wpersist_blocks(A0.L, A0.wv, A0.wgeo.threads, smem, &per_sm));
+    else {
+        CK(pstd::set_max_smem((int)smem));
+        CK(pstd::k_step_persist_blocks(smem, &per_sm));
+    }
+    if (per_sm < 1) return PSTD_EUNSUPPORTED;
+    int64_t grid = (int64_t)per_sm * nsm;
+    if (grid > most) grid = most;
+    if (grid < 1) grid = 1;
+    GridSync sync;
+    sync.count = S->d_sync;
+    sync.gen = S->d_sync + 1;
+    sync.status = (int*)(S->d_sync + 2);
+    sync.expected = (unsigned)grid + withhold;
+    sync.spin_limit = spin_limit > 0 ? spin_limit : 2000000LL;
+    if (kind == 1) {
+        PersistArgs pa{};
+        pa.ndim = npass;
+        pa.nsteps = nsteps;
+        pa.sync = sync;
+        pa.members = n;
+        pa.mem = (const WStep*)S->d_args;
+        pa.prefix = S->d_prefix;
+        WLaunch g;
+        g.grid = (unsigned)grid;
+        g.threads = A0.wgeo.threads;
+        g.smem = smem;
+        CK(wpersist(A0.L, A0.wv, g, st, pa));
+    } else {
+        StepPersistArgs sa;
+        sa.mem = (const StepArgs*)S->d_args;
+        sa.prefix = S->d_prefix;
+        sa.members = n;
+        sa.npass = npass;
+        sa.nsteps = nsteps;
+        CK(pstd::launch_k_step_persist((unsigned)grid, smem, st, sa, sync));
     }
     return PSTD_OK;
 }

@@ -617,9 +617,16 @@ PSTD_HD void tile_of(const WAxis& A, int64_t block, int64_t& o, int64_t& i0, int
     Gv = (int)(left < A.G ? left : A.G);
 }
 
-// Row stride in shared memory for a line of `len` words (odd: conflict-free
-// transposed staging).
-PSTD_HD int row_stride(int len) { return len | 1; }
+// Row stride in shared memory of a tile of G lines of `len` words each.  The
+// staging loops (tile_load / tile_store) put G consecutive threads on the G
+// lines of one position, so a warp covers 32 / G positions of every line; a
+// stride of 32 / G (mod 32) words puts its 32 words on 32 distinct banks
+// (G a power of two).  From G = 32 on (short lines, many per tile) an odd
+// stride does that at less padding.
+PSTD_HD int row_stride(int len, int G) {
+    if (G >= 32) return len | 1;
+    return len + ((32 / G - len) & 31);
+}
 
 // G is a power of two: item idx is (position idx >> log2 G, line idx & (G-1)).
 PSTD_HD int log2_pow2(int G) {
@@ -636,7 +643,7 @@ PSTD_HD int log2_pow2(int G) {
 // are enumerated directly.
 PSTD_HD void tile_load(const float* f, int len, const WAxis& A, int64_t o, int64_t i0, int Gv,
                        float* raw, int tid, int nthr) {
-    const int rs = row_stride(len);
+    const int rs = row_stride(len, A.G);
     const int gs = log2_pow2(A.G), gm = A.G - 1;
     const float* base = f + o * (int64_t)len * A.inner + i0;
     if ((nthr & gm) == 0) {
@@ -658,7 +665,7 @@ PSTD_HD void tile_load(const float* f, int len, const WAxis& A, int64_t o, int64
 
 PSTD_HD void tile_store(float* f, int len, const WAxis& A, int64_t o, int64_t i0, int Gv,
                         const float* raw, int tid, int nthr) {
-    const int rs = row_stride(len);
+    const int rs = row_stride(len, A.G);
     const int gs = log2_pow2(A.G), gm = A.G - 1;
     float* base = f + o * (int64_t)len * A.inner + i0;
     if ((nthr & gm) == 0) {
@@ -681,8 +688,8 @@ PSTD_HD void tile_store(float* f, int len, const WAxis& A, int64_t o, int64_t i0
 // shared memory of a strided step tile (without the staged tables), in floats
 PSTD_HD size_t strided_step_floats(const WAxis& A, int seq_words, bool separate_acc) {
     const size_t fft = (size_t)A.seqs * seq_words * 2;
-    const size_t p = (size_t)A.G * row_stride(A.lp);
-    const size_t u = (size_t)A.G * row_stride(A.N);
+    const size_t p = (size_t)A.G * row_stride(A.lp, A.G);
+    const size_t u = (size_t)A.G * row_stride(A.N, A.G);
     return fft + p + u + (separate_acc ? p : 0);
 }
 
@@ -702,8 +709,8 @@ PSTD_HD void step_strided(const WStep& a, int64_t block, float2* smem0, int tid,
     const int N = A.N, lp = A.lp;
     const bool sep = a.acc_in != a.p;
     float* rawP = (float*)(smem + (size_t)A.seqs * wf::seq_words<S::L>());
-    float* rawU = rawP + (size_t)A.G * row_stride(lp);
-    float* rawA = sep ? rawU + (size_t)A.G * row_stride(N) : rawP;
+    float* rawU = rawP + (size_t)A.G * row_stride(lp, A.G);
+    float* rawA = sep ? rawU + (size_t)A.G * row_stride(N, A.G) : rawP;
     pdl_wait();
     tile_load(a.p, lp, A, o, i0, Gv, rawP, tid, nthr);
     tile_load(a.u, N, A, o, i0, Gv, rawU, tid, nthr);
@@ -711,7 +718,7 @@ PSTD_HD void step_strided(const WStep& a, int64_t block, float2* smem0, int tid,
     // an odd tile's last line pairs with the phantom row Gv (< G)
     const bool phrow = A.ph && (Gv & 1);
     if (phrow)
-        for (int m = tid; m < N; m += nthr) rawU[Gv * row_stride(N) + m] = A.ph[o * N + m];
+        for (int m = tid; m < N; m += nthr) rawU[Gv * row_stride(N, A.G) + m] = A.ph[o * N + m];
     async_wait_all();
     PSTD_SYNCCTA();
     if (sq < A.seqs) {
@@ -719,10 +726,10 @@ PSTD_HD void step_strided(const WStep& a, int64_t block, float2* smem0, int tid,
         const bool va = ga < Gv, vb = gb < Gv;
         const bool vbu = vb || (phrow && gb == Gv);
         float2* sm = smem + (size_t)sq * wf::seq_words<S::L>();
-        const float* pa = rawP + (va ? ga : 0) * row_stride(lp);
-        const float* pb = rawP + (vb ? gb : 0) * row_stride(lp);
-        float* ua = rawU + (va ? ga : 0) * row_stride(N);
-        float* ub = rawU + (vbu ? gb : 0) * row_stride(N);
+        const float* pa = rawP + (va ? ga : 0) * row_stride(lp, A.G);
+        const float* pb = rawP + (vb ? gb : 0) * row_stride(lp, A.G);
+        float* ua = rawU + (va ? ga : 0) * row_stride(N, A.G);
+        float* ub = rawU + (vbu ? gb : 0) * row_stride(N, A.G);
         float2 v[E];
         load_p_ext<S>(v, t, A, tab, [&](int i) { return make_float2(va ? pa[i] : 0.0f, vb ? pb[i] : 0.0f); });
         fft<S, false>(v, t, sm, tab);
@@ -735,8 +742,8 @@ PSTD_HD void step_strided(const WStep& a, int64_t block, float2* smem0, int tid,
             if (va) ua[s] = x.x;
             if (vbu) ub[s] = x.y;
         });
-        float* aa = rawA + (va ? ga : 0) * row_stride(lp);
-        float* ab = rawA + (vb ? gb : 0) * row_stride(lp);
+        float* aa = rawA + (va ? ga : 0) * row_stride(lp, A.G);
+        float* ab = rawA + (vb ? gb : 0) * row_stride(lp, A.G);
         seq_sync<S>();
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -751,7 +758,7 @@ PSTD_HD void step_strided(const WStep& a, int64_t block, float2* smem0, int tid,
     tile_store(a.u, N, A, o, i0, Gv, rawU, tid, nthr);
     tile_store(a.acc_out, lp, A, o, i0, Gv, rawA, tid, nthr);
     if (phrow)
-        for (int m = tid; m < N; m += nthr) A.ph[o * N + m] = rawU[Gv * row_stride(N) + m];
+        for (int m = tid; m < N; m += nthr) A.ph[o * N + m] = rawU[Gv * row_stride(N, A.G) + m];
     pdl_trigger();
 }
 
@@ -772,7 +779,7 @@ PSTD_HD void grad_strided(const WGrad& a, int64_t block, float2* smem0, int tid,
     const int nin = from_p ? A.lp : A.N;
     const int nout = a.dir == 0 || a.dir == 2 || a.dir == 3 ? A.N : A.lp;
     float* rawI = (float*)(smem + (size_t)A.seqs * wf::seq_words<S::L>());
-    float* rawO = rawI + (size_t)A.G * row_stride(nin);
+    float* rawO = rawI + (size_t)A.G * row_stride(nin, A.G);
     pdl_wait();
     tile_load(a.in, nin, A, o, i0, Gv, rawI, tid, nthr);
     if (a.accumulate) tile_load(a.out, nout, A, o, i0, Gv, rawO, tid, nthr);
@@ -784,7 +791,7 @@ PSTD_HD void grad_strided(const WGrad& a, int64_t block, float2* smem0, int tid,
         // from WAxis::ph (dir 3) or written to it (dir 2).
         const bool phrow = A.ph && (Gv & 1);
         if (phrow && a.dir == 3) {
-            for (int m = tid; m < A.N; m += nthr) rawI[Gv * row_stride(nin) + m] = A.ph[o * A.N + m];
+            for (int m = tid; m < A.N; m += nthr) rawI[Gv * row_stride(nin, A.G) + m] = A.ph[o * A.N + m];
             PSTD_SYNCCTA();
         }
         if (sq < A.seqs) {
@@ -793,10 +800,10 @@ PSTD_HD void grad_strided(const WGrad& a, int64_t block, float2* smem0, int tid,
             const bool ph = phrow && gb == Gv;
             const bool rb = vb || (ph && a.dir == 3), wb = vb || (ph && a.dir == 2);
             float2* sm = smem + (size_t)sq * wf::seq_words<S::L>();
-            const float* xa = rawI + (va ? ga : 0) * row_stride(nin);
-            const float* xb = rawI + (rb ? gb : 0) * row_stride(nin);
-            float* oa = rawO + (va ? ga : 0) * row_stride(nout);
-            float* ob = rawO + (wb ? gb : 0) * row_stride(nout);
+            const float* xa = rawI + (va ? ga : 0) * row_stride(nin, A.G);
+            const float* xb = rawI + (rb ? gb : 0) * row_stride(nin, A.G);
+            float* oa = rawO + (va ? ga : 0) * row_stride(nout, A.G);
+            float* ob = rawO + (wb ? gb : 0) * row_stride(nout, A.G);
             spec_convert<S>(a.dir, a.scale, t, sm, A, tab,
                             [&](int i) { return make_float2(va ? xa[i] : 0.0f, rb ? xb[i] : 0.0f); },
                             [&](int i, float2 x) {
@@ -807,25 +814,25 @@ PSTD_HD void grad_strided(const WGrad& a, int64_t block, float2* smem0, int tid,
         PSTD_SYNCCTA();
         tile_store(a.out, nout, A, o, i0, Gv, rawO, tid, nthr);
         if (phrow && a.dir == 2)
-            for (int m = tid; m < A.N; m += nthr) A.ph[o * A.N + m] = rawO[Gv * row_stride(nout) + m];
+            for (int m = tid; m < A.N; m += nthr) A.ph[o * A.N + m] = rawO[Gv * row_stride(nout, A.G) + m];
         return;
     }
     if (sq < A.seqs) {
         const int ga = 2 * sq, gb = 2 * sq + 1;
         const bool va = ga < Gv, vb = gb < Gv;
         float2* sm = smem + (size_t)sq * wf::seq_words<S::L>();
-        const float* xa = rawI + (va ? ga : 0) * row_stride(nin);
-        const float* xb = rawI + (vb ? gb : 0) * row_stride(nin);
+        const float* xa = rawI + (va ? ga : 0) * row_stride(nin, A.G);
+        const float* xb = rawI + (vb ? gb : 0) * row_stride(nin, A.G);
         float2 v[E];
         auto src = [&](int i) { return make_float2(va ? xa[i] : 0.0f, vb ? xb[i] : 0.0f); };
         if (from_p) derivative<S, 0>(v, t, sm, A, tab, src);
         else derivative<S, 1>(v, t, sm, A, tab, src);
-        float* oa = rawO + (va ? ga : 0) * row_stride(nout);
-        float* ob = rawO + (vb ? gb : 0) * row_stride(nout);
+        float* oa = rawO + (va ? ga : 0) * row_stride(nout, A.G);
+        float* ob = rawO + (vb ? gb : 0) * row_stride(nout, A.G);
         // dir 4 with pout: the input rows become in + out in place (this
         // sequence's reads of them precede the FFT's barriers)
-        float* ia = rawI + (va ? ga : 0) * row_stride(nin);
-        float* ib = rawI + (vb ? gb : 0) * row_stride(nin);
+        float* ia = rawI + (va ? ga : 0) * row_stride(nin, A.G);
+        float* ib = rawI + (vb ? gb : 0) * row_stride(nin, A.G);
         const int off = a.dir == 0 ? 0 : A.lo;
 #pragma unroll
         for (int e = 0; e < E; ++e) {

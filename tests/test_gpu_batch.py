@@ -9,6 +9,7 @@ from paper_2005_00322_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 DX = 1e-4
+BCS4 = [("N", "N"), ("N", "D"), ("D", "N"), ("D", "D")]
 
 
 def _oracle_member(ncells, bc, cfl, p_full, steps):
@@ -89,3 +90,99 @@ def test_reflection_2d_matches_oracle(refl):
     err = np.linalg.norm(got - ref) / np.linalg.norm(p_full)
     assert err < 1e-4, err
     R.batch.close()
+
+
+def _batch_fields(B, seed):
+    fields = B.zeros()
+    for m, (p, _) in enumerate(fields):
+        p.copy_(torch.tensor(inputs.random_field(B.shapes[m][0], seed + m).astype(np.float32)))
+    return fields
+
+
+def _clone(fields):
+    return [(p.clone(), [u.clone() for u in us]) for p, us in fields]
+
+
+def test_persistent_batch_register_kernel_equals_graph():
+    """The 16 wall combinations of one 2-D grid share every register-FFT
+    schedule: one cooperative kernel runs all members' passes, bit for bit the
+    graph path's result, with one launch per run plus the conversions."""
+    from paper_2005_00322_gb300.batch import Batch
+    bcs = [(a, b) for a in BCS4 for b in BCS4]
+    members = [dict(ncells=(128, 128), dx=DX, bc=list(bc), cfl=0.2) for bc in bcs]
+    A, B = Batch(members), Batch(members)
+    B.set_persistent()
+    assert B.persistent_kind() == "register"
+    fa = _batch_fields(A, 60)
+    A.init_velocity(fa)
+    fb = _clone(fa)
+    A.run(fa, 70)
+    B.run(fb, 70)
+    A.sync()
+    B.sync()
+    conv = B.last_launch_count() - 1
+    assert 0 < conv <= 2 * 2 * len(members)
+    for (pa, ua), (pb, ub) in zip(fa, fb):
+        assert torch.equal(pa, pb)
+        assert all(torch.equal(x, y) for x, y in zip(ua, ub))
+    A.close()
+    B.close()
+
+
+def test_persistent_batch_generic_kernel_matches_graph():
+    """Uneven members (convolution, dense, generic-FFT and register-FFT axes,
+    1-D to 3-D) in one cooperative kernel on the generic CTA program: members
+    whose axes all take that program in the graph path too agree bit for bit;
+    a register-FFT axis computed by the generic program agrees to rounding."""
+    from paper_2005_00322_gb300.batch import Batch
+    specs = [((100, 70), [("D", "D"), ("N", "D")]), ((37, 130), [("N", "N"), ("D", "N")]),
+             ((128,), [("D", "N")]), ((96, 50), [("N", "D"), ("D", "D")]),
+             ((20, 18, 27), [("N", "D"), ("D", "D"), ("N", "N")])]
+    members = [dict(ncells=n, dx=DX, bc=b, cfl=0.2) for n, b in specs]
+    A, B = Batch(members), Batch(members)
+    B.set_persistent()
+    assert B.persistent_kind() == "generic"
+    fa = _batch_fields(A, 80)
+    A.init_velocity(fa)
+    fb = _clone(fa)
+    A.run(fa, 45)
+    B.run(fb, 45)
+    A.sync()
+    B.sync()
+    assert B.last_launch_count() == 1
+    from paper_2005_00322_gb300 import Solver
+    for m, ((pa, ua), (pb, ub)) in enumerate(zip(fa, fb)):
+        s = Solver(specs[m][0], DX, specs[m][1], cfl=0.2)
+        register = any(sc[0] >= 0 for sc in s.schedule())
+        s.close()
+        if not register:
+            assert torch.equal(pa, pb), m
+            assert all(torch.equal(x, y) for x, y in zip(ua, ub)), m
+        else:
+            assert ((pa - pb).norm() / pa.norm()).item() < 1e-5, m
+            assert all(((x - y).norm() / x.norm()).item() < 1e-5 for x, y in zip(ua, ub)), m
+    A.close()
+    B.close()
+
+
+def test_persistent_batch_stalled_barrier_reports_timeout():
+    """A barrier that waits for one arrival too many gives up after the poll
+    limit: pstd_batch_sync reports PSTD_ETIMEOUT once and the batch runs again."""
+    from paper_2005_00322_gb300._abi import PstdError
+    from paper_2005_00322_gb300.batch import Batch
+    members = [dict(ncells=(100, 70), dx=DX, bc=[("D", "D"), ("N", "D")], cfl=0.2),
+               dict(ncells=(64, 48), dx=DX, bc=[("N", "N"), ("D", "D")], cfl=0.2)]
+    B = Batch(members)
+    B.set_persistent(spin_limit=1000, withhold_arrivals=1)
+    f = _batch_fields(B, 90)
+    B.run(f, 5)
+    with pytest.raises(PstdError, match="ETIMEOUT"):
+        B.sync()
+    B.sync()
+    B.set_persistent(spin_limit=0, withhold_arrivals=0)
+    g = _batch_fields(B, 90)
+    B.init_velocity(g)
+    B.run(g, 5)
+    B.sync()
+    assert all(torch.isfinite(p).all() for p, _ in g)
+    B.close()
