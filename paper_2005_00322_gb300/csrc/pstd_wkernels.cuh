@@ -47,9 +47,11 @@ __global__ void __launch_bounds__(256) k_wgrad_s(WGrad a) {
     wk::grad_strided<wf::Sched<L, V>>(a, blockIdx.x, wsm, threadIdx.x, blockDim.x);
 }
 
-// One cooperative launch for a whole run (pstd_persist.cuh).
+// One cooperative launch for a whole run (pstd_persist.cuh).  It holds both
+// pass kinds: the table-in-memory schedules (V = 4, 5) fit 3 CTAs per SM
+// without spilling, the others keep their full register budget.
 template <int L, int V>
-__global__ void __launch_bounds__(256) k_persist(PersistArgs a) {
+__global__ void __launch_bounds__(256, V >= 4 ? 3 : 1) k_persist(PersistArgs a) {
     extern __shared__ float4 wsm4[];
     persistent_run<wf::Sched<L, V>>(a, (float2*)wsm4);
 }
