@@ -837,12 +837,14 @@ int build_axis(pstd_plan_s* P, int i) {
     int V = 0;
     int os = P->opts.seqs_per_cta[i];
     const int ov = P->opts.variant[i];
+    // the table-in-memory schedules (4, 5) are compiled for walled axes,
+    // L = 2 N (their passes fix N = L / 2)
     if (ov == 5) {
-        if (pstd::wlanes_v5(a.L) == 0) return PSTD_EINVAL;
+        if (pstd::wlanes_v5(a.L) == 0 || a.periodic) return PSTD_EINVAL;
         V = 5;
         T = pstd::wlanes_v5(a.L);
     } else if (ov == 4) {
-        if (pstd::wlanes_v4(a.L) == 0) return PSTD_EINVAL;
+        if (pstd::wlanes_v4(a.L) == 0 || a.periodic) return PSTD_EINVAL;
         V = 4;
         T = pstd::wlanes_v4(a.L);
     } else if (ov == 3) {
@@ -871,7 +873,7 @@ int build_axis(pstd_plan_s* P, int i) {
     // shared memory (V=4) holds 80 instead of 128 registers, so 3 CTAs of 256
     // threads fit per SM; measured 0.660 -> 0.572 ms per 256^3 step, with 4
     // line pairs per CTA on every axis
-    if (ov < 0 && V == 1 && pstd::wlanes_v4(a.L) > 0 && (a.nlines + 1) / 2 >= 4 * 2 * nsm) {
+    if (ov < 0 && V == 1 && !a.periodic && pstd::wlanes_v4(a.L) > 0 && (a.nlines + 1) / 2 >= 4 * 2 * nsm) {
         V = 4;
         T = pstd::wlanes_v4(a.L);
     }

@@ -276,6 +276,18 @@ constexpr bool staged_tables() {
     return !reg_tables<S>() && S::V != 5;
 }
 
+// The table-in-memory schedules (V >= 4) serve only walled axes, L = 2 N:
+// fixing N and L in the pass's copy of the axis turns the index logic of the
+// extension and of the spectrum slots (bin k = t + T e against N) into
+// compile-time branches on e.
+template <class S>
+PSTD_HD void fix_extent(WAxis& A) {
+    if constexpr (S::V >= 4) {
+        A.L = S::L;
+        A.N = S::L / 2;
+    }
+}
+
 // Tables of one derivative for schedule S (registers for the latency
 // schedules, direct access otherwise).
 template <class S>
@@ -408,6 +420,7 @@ PSTD_HD void step_contig(const WStep& a, int64_t block, float2* smem, int tid, i
     int sq, t;
     lane_of<S>(tid, sq, t);
     WAxis A = a.ax;
+    fix_extent<S>(A);
     const float2* fP = a.fP;
     const float2* fU = a.fU;
     float2* bufs = stage_tables<S>(A, fP, fU, smem, tid, nthr);
@@ -617,15 +630,13 @@ PSTD_HD void tile_of(const WAxis& A, int64_t block, int64_t& o, int64_t& i0, int
     Gv = (int)(left < A.G ? left : A.G);
 }
 
-// Row stride in shared memory of a tile of G lines of `len` words each.  The
-// staging loops (tile_load / tile_store) put G consecutive threads on the G
-// lines of one position, so a warp covers 32 / G positions of every line; a
-// stride of 32 / G (mod 32) words puts its 32 words on 32 distinct banks
-// (G a power of two).  From G = 32 on (short lines, many per tile) an odd
-// stride does that at less padding.
+// Row stride in shared memory of a tile of G lines of `len` words each: odd.
+// (A stride of 32 / G (mod 32) words would put the 32 words of a warp's
+// staging copies on distinct banks, but measured slower on 256^3: 0.602
+// against 0.570 ms per step.)
 PSTD_HD int row_stride(int len, int G) {
-    if (G >= 32) return len | 1;
-    return len + ((32 / G - len) & 31);
+    (void)G;
+    return len | 1;
 }
 
 // G is a power of two: item idx is (position idx >> log2 G, line idx & (G-1)).
@@ -697,6 +708,7 @@ template <class S>
 PSTD_HD void step_strided(const WStep& a, int64_t block, float2* smem0, int tid, int nthr) {
     constexpr int T = S::T, E = S::E;
     WAxis A = a.ax;
+    fix_extent<S>(A);
     const float2* fP = a.fP;
     const float2* fU = a.fU;
     float2* smem = stage_tables<S>(A, fP, fU, smem0, tid, nthr);

@@ -133,6 +133,9 @@ def test_unavailable_variant_is_rejected():
     from paper_2005_00322_gb300._abi import PstdError
     with pytest.raises(PstdError, match="EINVAL"):
         Solver((96, 64), DX, [("N", "N"), ("D", "D")], cfl=0.2, schedule=[(4, 1), None])   # L = 192
+    with pytest.raises(PstdError, match="EINVAL"):
+        # the table-in-memory schedules serve walled axes only
+        Solver((256, 64), DX, [("P", "P"), ("N", "N")], cfl=0.2, schedule=[(5, 1), None])
 
 
 @pytest.mark.parametrize("ncells,bcs", CASES[:8])
