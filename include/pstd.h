@@ -113,8 +113,10 @@ typedef struct pstd_plan_s pstd_plan_t;
  * powers of two, 96, 192, 384, 768}; shared-memory Stockham FFT passes for
  * other M with prime factors 2, 3 and 5 only; for any other M, a dense
  * operator matrix when N_i <= 64, else a (skew-)circular convolution of
- * length M evaluated as a power-of-two linear convolution (FFT length up to
- * 8192, i.e. M up to 4096; longer such axes return PSTD_EUNSUPPORTED).
+ * length M evaluated as a linear convolution through a circular FFT of
+ * length M2 >= 2M - 1: of the 2^a 3^b 5^c lengths up to the next power of
+ * two, the one with the least Stockham traffic (M2 x passes).  M2 is at most
+ * 8192, i.e. M up to 4096; longer such axes return PSTD_EUNSUPPORTED.
  * `stream` is a cudaStream_t (NULL = legacy default stream).
  * Errors: PSTD_EINVAL (ndim, N_i, dx, c0, rho0, dt, bc or uinit out of
  * range; N_i = 1 with DD walls has no pressure node), PSTD_EUNSTABLE,
