@@ -869,24 +869,26 @@ int build_axis(pstd_plan_s* P, int i) {
         V = 3;
         T = pstd::wlanes_v3(a.L);
     }
-    // many lines (the 3-D sizes): the latency schedule with its tables in
-    // shared memory (V=4) holds 80 instead of 128 registers, so 3 CTAs of 256
-    // threads fit per SM; measured 0.660 -> 0.572 ms per 256^3 step, with 4
-    // line pairs per CTA on every axis
+    // many lines (the 3-D sizes), walled axes: the latency radices with the
+    // tables read from memory instead of registers (V=5: global through L1,
+    // 64 registers; V=4 at 768: shared memory) and N = L / 2 fixed at compile
+    // time; measured on 256^3 0.660 (V=1) -> 0.572 (V=4) -> 0.482 ms per step
+    // (V=5, 4 line pairs per CTA on strided axes, 1 on the contiguous one)
     if (ov < 0 && V == 1 && !a.periodic && pstd::wlanes_v4(a.L) > 0 && (a.nlines + 1) / 2 >= 4 * 2 * nsm) {
-        V = 4;
-        T = pstd::wlanes_v4(a.L);
+        V = pstd::wlanes_v5(a.L) > 0 ? 5 : 4;
+        T = V == 5 ? pstd::wlanes_v5(a.L) : pstd::wlanes_v4(a.L);
     }
     if (os == 0 || os > 256 || (os > 0 && (os & (os - 1)))) return PSTD_EINVAL;
     const bool auto_os = os < 0;
     if (os < 0 && V >= 1 && T <= 128 && (a.nlines + 1) / 2 >= 2 * 2 * nsm) os = 2;
     // strided axes stage tiles of 2 os lines: 4 sequences make each staged
     // run 8 words (one 32-byte sector); measured 0.815 -> 0.768 ms per 256^3
-    // step.  The shared-table schedule takes 4 on contiguous axes too.  Not
+    // step.  The shared-table schedule takes 4 on contiguous axes too, the
+    // global-table one 1 (64-thread CTAs, 16 per SM).  Not
     // for the persistent run, whose axes share one CTA size.
     if (auto_os && os == 2 && !P->opts.persistent && (inner > 1 || V >= 4) && T <= 64 &&
         (a.nlines + 1) / 2 >= 4 * 2 * nsm)
-        os = 4;
+        os = inner == 1 && V == 5 ? 1 : 4;
     if (a.kind == 0 && T > 0) {
         std::vector<float2> wt;
         if (!wtw(a.L, V, wt)) return PSTD_EUNSUPPORTED;

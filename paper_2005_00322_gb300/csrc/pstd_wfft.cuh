@@ -156,6 +156,7 @@ PSTD_SCHED(256, 4, 32, 8, 8, 4)
 PSTD_SCHED(512, 4, 64, 8, 8, 8)
 PSTD_SCHED(256, 5, 32, 8, 8, 4)
 PSTD_SCHED(512, 5, 64, 8, 8, 8)
+PSTD_SCHED(768, 4, 64, 4, 4, 4, 4, 3)
 #undef PSTD_SCHED
 
 // Ns before pass p (product of earlier radices)

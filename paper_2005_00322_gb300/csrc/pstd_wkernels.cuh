@@ -12,10 +12,11 @@ namespace pstd {
 
 // Resident CTAs of 256 threads per SM that a pass kernel is compiled for:
 // the latency passes of the 3-D sizes (L <= 768) run at 128 registers, their
-// shared-table form (V = 4) at 80 and their global-table form (V = 5) at 64.
+// shared-table form (V = 4) at 80 (768: 128, 12 elements per lane) and their
+// global-table form (V = 5) at 64.
 template <int L, int V>
 constexpr int wmin_blocks() {
-    return V == 5 ? 4 : V == 4 ? 3 : (V == 1 && L <= 768) ? 2 : 1;
+    return V == 5 ? 4 : V == 4 ? (L == 768 ? 2 : 3) : (V == 1 && L <= 768) ? 2 : 1;
 }
 
 // The contiguous latency pass of the 3-D sizes (L <= 768, the lean form of
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(256) k_wgrad_s(WGrad a) {
 // pass kinds: the table-in-memory schedules (V = 4, 5) fit 3 CTAs per SM
 // without spilling, the others keep their full register budget.
 template <int L, int V>
-__global__ void __launch_bounds__(256, V >= 4 ? 3 : 1) k_persist(PersistArgs a) {
+__global__ void __launch_bounds__(256, V >= 4 ? (L == 768 ? 2 : 3) : 1) k_persist(PersistArgs a) {
     extern __shared__ float4 wsm4[];
     persistent_run<wf::Sched<L, V>>(a, (float2*)wsm4);
 }
@@ -167,9 +168,9 @@ void wtwiddles(std::vector<float2>& out) {
 inline int wlanes_v2(int L) { return L == 1024 ? 64 : 0; }
 // Lanes per sequence of Sched<L, 4> (the latency radices, tables in shared
 // memory; 0: none).
-inline int wlanes_v4(int L) { return L == 512 ? 64 : (L == 256 ? 32 : 0); }
+inline int wlanes_v4(int L) { return L == 512 || L == 768 ? 64 : (L == 256 ? 32 : 0); }
 // Lanes per sequence of Sched<L, 5> (as V = 4, tables read from global memory).
-inline int wlanes_v5(int L) { return wlanes_v4(L); }
+inline int wlanes_v5(int L) { return L == 512 ? 64 : (L == 256 ? 32 : 0); }
 // Lanes per sequence of Sched<L, 3> (more lanes, 4 elements each; 0: none).
 inline int wlanes_v3(int L) { return L == 1024 ? 256 : (L == 512 ? 128 : 0); }
 
