@@ -133,7 +133,7 @@ int pstd_plan(const pstd_desc* desc, void* stream, pstd_plan_t** out);
  * twiddle tables read from shared memory instead of registers (fewer
  * registers per thread, more resident CTAs), variant 5 (lengths 256, 512)
  * the same with the tables read from global memory through L1 (neither
- * registers nor shared memory hold them); variants 4 and 5 serve walled
+ * registers nor shared memory hold them); variants 3, 4 and 5 serve walled
  * (non-periodic) axes only.  An unavailable variant gives PSTD_EINVAL.
  * seqs_per_cta: line pairs per CTA (a power of two). */
 typedef struct {

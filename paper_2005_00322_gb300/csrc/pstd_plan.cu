@@ -837,8 +837,8 @@ int build_axis(pstd_plan_s* P, int i) {
     int V = 0;
     int os = P->opts.seqs_per_cta[i];
     const int ov = P->opts.variant[i];
-    // the table-in-memory schedules (4, 5) are compiled for walled axes,
-    // L = 2 N (their passes fix N = L / 2)
+    // schedules 3, 4 and 5 are compiled for walled axes, L = 2 N (their
+    // passes fix N = L / 2)
     if (ov == 5) {
         if (pstd::wlanes_v5(a.L) == 0 || a.periodic) return PSTD_EINVAL;
         V = 5;
@@ -848,7 +848,7 @@ int build_axis(pstd_plan_s* P, int i) {
         V = 4;
         T = pstd::wlanes_v4(a.L);
     } else if (ov == 3) {
-        if (pstd::wlanes_v3(a.L) == 0) return PSTD_EINVAL;
+        if (pstd::wlanes_v3(a.L) == 0 || a.periodic) return PSTD_EINVAL;
         V = 3;
         T = pstd::wlanes_v3(a.L);
     } else if (ov == 2) {
@@ -865,7 +865,7 @@ int build_axis(pstd_plan_s* P, int i) {
     // per 512^2 step and 14.2 -> 9.3 us per 256^2 step (with many lines, as
     // in 256^3, the 8-element schedule stays faster: 0.69 vs 0.94 ms)
     const int64_t nsm = P->nsm;
-    if (ov < 0 && V == 1 && pstd::wlanes_v3(a.L) > 0 && (a.nlines + 1) / 2 < 2 * 2 * nsm) {
+    if (ov < 0 && V == 1 && !a.periodic && pstd::wlanes_v3(a.L) > 0 && (a.nlines + 1) / 2 < 2 * 2 * nsm) {
         V = 3;
         T = pstd::wlanes_v3(a.L);
     }

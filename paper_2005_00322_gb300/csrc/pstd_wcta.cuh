@@ -276,13 +276,13 @@ constexpr bool staged_tables() {
     return !reg_tables<S>() && S::V != 5;
 }
 
-// The table-in-memory schedules (V >= 4) serve only walled axes, L = 2 N:
-// fixing N and L in the pass's copy of the axis turns the index logic of the
-// extension and of the spectrum slots (bin k = t + T e against N) into
-// compile-time branches on e.
+// Schedules 3, 4 and 5 serve only walled axes, L = 2 N: fixing N and L in
+// the pass's copy of the axis turns the index logic of the extension and of
+// the spectrum slots (bin k = t + T e against N) into compile-time branches
+// on e.
 template <class S>
 PSTD_HD void fix_extent(WAxis& A) {
-    if constexpr (S::V >= 4) {
+    if constexpr (S::V >= 3) {
         A.L = S::L;
         A.N = S::L / 2;
     }
