@@ -247,7 +247,7 @@ PSTD_HD void fft_pass(const FftPlan& P, int p, int& Ns, const float2* src, float
 // Build the extension of line pairs (2s, 2s+1) from raw into buf (FFT route).
 PSTD_HD void phase_extend(const LineOp& op, const float* raw, int rs, int G, float2* buf,
                           int tid, int nthr) {
-    const int L = op.L, N = op.N, SL = op.seqlen;
+    const int L = op.L, SL = op.seqlen;
     const int nseq = (G + 1) / 2;
     const int total = nseq * SL;
     for (int t = tid; t < total; t += nthr) {

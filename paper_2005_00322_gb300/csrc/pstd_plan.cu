@@ -47,12 +47,36 @@ cudaError_t wsmall_smem(int L, int V, int bytes);
 bool wsmall_twiddles(int L, int V, std::vector<float2>& out);
 cudaError_t wsmall_persist(int L, int V, const WLaunch& g, cudaStream_t st, const PersistArgs& a);
 cudaError_t wsmall_persist_blocks(int L, int V, int threads, size_t smem, int* blocks);
+cudaError_t w64_step(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WStep& a);
+cudaError_t w64_grad(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WGrad& a);
+cudaError_t w64_smem(int L, int V, int bytes);
+bool w64_twiddles(int L, int V, std::vector<float2>& out);
+cudaError_t w64_persist(int L, int V, const WLaunch& g, cudaStream_t st, const PersistArgs& a);
+cudaError_t w64_persist_blocks(int L, int V, int threads, size_t smem, int* blocks);
+cudaError_t w1024t_step(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WStep& a);
+cudaError_t w1024t_grad(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WGrad& a);
+cudaError_t w1024t_smem(int L, int V, int bytes);
+bool w1024t_twiddles(int L, int V, std::vector<float2>& out);
+cudaError_t w1024t_persist(int L, int V, const WLaunch& g, cudaStream_t st, const PersistArgs& a);
+cudaError_t w1024t_persist_blocks(int L, int V, int threads, size_t smem, int* blocks);
+cudaError_t w256_step(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WStep& a);
+cudaError_t w256_grad(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WGrad& a);
+cudaError_t w256_smem(int L, int V, int bytes);
+bool w256_twiddles(int L, int V, std::vector<float2>& out);
+cudaError_t w256_persist(int L, int V, const WLaunch& g, cudaStream_t st, const PersistArgs& a);
+cudaError_t w256_persist_blocks(int L, int V, int threads, size_t smem, int* blocks);
 cudaError_t w512_step(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WStep& a);
 cudaError_t w512_grad(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WGrad& a);
 cudaError_t w512_smem(int L, int V, int bytes);
 bool w512_twiddles(int L, int V, std::vector<float2>& out);
 cudaError_t w512_persist(int L, int V, const WLaunch& g, cudaStream_t st, const PersistArgs& a);
 cudaError_t w512_persist_blocks(int L, int V, int threads, size_t smem, int* blocks);
+cudaError_t w768_step(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WStep& a);
+cudaError_t w768_grad(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WGrad& a);
+cudaError_t w768_smem(int L, int V, int bytes);
+bool w768_twiddles(int L, int V, std::vector<float2>& out);
+cudaError_t w768_persist(int L, int V, const WLaunch& g, cudaStream_t st, const PersistArgs& a);
+cudaError_t w768_persist_blocks(int L, int V, int threads, size_t smem, int* blocks);
 cudaError_t w1024_step(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WStep& a);
 cudaError_t w1024_grad(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WGrad& a);
 cudaError_t w1024_smem(int L, int V, int bytes);
@@ -142,37 +166,35 @@ struct Axis {
     size_t gsmem = 0;
 };
 
-// register-FFT dispatch by length and schedule variant
+// register-FFT dispatch by length and schedule variant: the translation unit
+// that instantiates (L, V)
+#define PSTD_WBY_LENGTH(CALL)                      \
+    switch (L) {                                   \
+        case 1024:                                 \
+            if (V == 0 || V == 2) return pstd::w1024t_##CALL; \
+            return pstd::w1024_##CALL;             \
+        case 768: case 384: return pstd::w768_##CALL; \
+        case 512: return pstd::w512_##CALL;        \
+        case 256: return pstd::w256_##CALL;        \
+        case 64: case 128: case 96: case 192:      \
+            return pstd::w64_##CALL;               \
+        default: return pstd::wsmall_##CALL;       \
+    }
 cudaError_t wstep(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WStep& a) {
-    if (L >= 1024 || L == 768) return pstd::w1024_step(L, V, s, g, st, a);
-    if (L == 512 || L == 384) return pstd::w512_step(L, V, s, g, st, a);
-    return pstd::wsmall_step(L, V, s, g, st, a);
+    PSTD_WBY_LENGTH(step(L, V, s, g, st, a))
 }
 cudaError_t wgrad(int L, int V, bool s, const WLaunch& g, cudaStream_t st, const WGrad& a) {
-    if (L >= 1024 || L == 768) return pstd::w1024_grad(L, V, s, g, st, a);
-    if (L == 512 || L == 384) return pstd::w512_grad(L, V, s, g, st, a);
-    return pstd::wsmall_grad(L, V, s, g, st, a);
+    PSTD_WBY_LENGTH(grad(L, V, s, g, st, a))
 }
-cudaError_t wsmem(int L, int V, int bytes) {
-    if (L >= 1024 || L == 768) return pstd::w1024_smem(L, V, bytes);
-    if (L == 512 || L == 384) return pstd::w512_smem(L, V, bytes);
-    return pstd::wsmall_smem(L, V, bytes);
-}
+cudaError_t wsmem(int L, int V, int bytes) { PSTD_WBY_LENGTH(smem(L, V, bytes)) }
 cudaError_t wpersist(int L, int V, const WLaunch& g, cudaStream_t st, const pstd::PersistArgs& a) {
-    if (L >= 1024 || L == 768) return pstd::w1024_persist(L, V, g, st, a);
-    if (L == 512 || L == 384) return pstd::w512_persist(L, V, g, st, a);
-    return pstd::wsmall_persist(L, V, g, st, a);
+    PSTD_WBY_LENGTH(persist(L, V, g, st, a))
 }
 cudaError_t wpersist_blocks(int L, int V, int threads, size_t smem, int* blocks) {
-    if (L >= 1024 || L == 768) return pstd::w1024_persist_blocks(L, V, threads, smem, blocks);
-    if (L == 512 || L == 384) return pstd::w512_persist_blocks(L, V, threads, smem, blocks);
-    return pstd::wsmall_persist_blocks(L, V, threads, smem, blocks);
+    PSTD_WBY_LENGTH(persist_blocks(L, V, threads, smem, blocks))
 }
-bool wtw(int L, int V, std::vector<float2>& out) {
-    if (L >= 1024 || L == 768) return pstd::w1024_twiddles(L, V, out);
-    if (L == 512 || L == 384) return pstd::w512_twiddles(L, V, out);
-    return pstd::wsmall_twiddles(L, V, out);
-}
+bool wtw(int L, int V, std::vector<float2>& out) { PSTD_WBY_LENGTH(twiddles(L, V, out)) }
+#undef PSTD_WBY_LENGTH
 
 struct GraphEntry {
     int kind = 0;                     // 0: leapfrog steps (u: velocities), 1: second-order steps (u[0]: q)
@@ -293,7 +315,7 @@ int upload(const std::vector<T>& h, T** d) {
 // Dense operator (rows: stored outputs, cols: stored inputs) of the same
 // multiplier, FP64, for axes with no FFT schedule.
 std::vector<double> dense_operator64(const Axis& a, int dir, double scale) {
-    const int N = a.N, L = a.L;
+    const int L = a.L;
     std::vector<std::complex<double>> K(L);
     for (int d = 0; d < L; ++d) {
         std::complex<double> acc = 0;
@@ -560,7 +582,7 @@ std::vector<std::complex<double>> conv_table_of(const Axis& a, const std::vector
 // f between two field kinds (as dense_operator64).
 std::vector<float> dense_operator_of(const Axis& a, const std::vector<std::complex<double>>& f, const KindGeo& gi,
                                      const KindGeo& go) {
-    const int N = a.N, L = a.L;
+    const int L = a.L;
     std::vector<std::complex<double>> K(L);
     for (int d = 0; d < L; ++d) {
         std::complex<double> acc = 0;
