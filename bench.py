@@ -430,7 +430,7 @@ def learned_main(args) -> None:
     (inputs.sno_initial_pressures); 20k training samples (seed 1), 1k test
     samples (seed 2) and 512 held-out samples (seed 3) that set the gate.  The
     network (4 layers, 32 channels, 16 modes per axis) trains on PSTD answers.
-    The solver is the judge: requests whose content above the 16th mode is too
+    The solver is the arbiter: requests whose content above the 16th mode is too
     large for the network (gate set on the held-out set at tolerance 1e-2
     relative L2) are answered by PSTD.  Reported: the network's error on the
     whole test set, the share of it the gate admits and their worst error, and
@@ -523,7 +523,7 @@ def learned_main(args) -> None:
         "accuracy": {"test": nte, "max_rel_l2": float(err.max()), "median_rel_l2": float(np.median(err)),
                      "share_within_tol": float((err <= 1e-2).mean()),
                      "admitted_max_rel_l2": float(err[admitted].max()) if admitted.any() else None,
-                     "judge": "PSTD on the same inputs"},
+                     "arbiter": "PSTD on the same inputs"},
         "gate": {"tol": sur.tol, "high_mode_fraction_below": sur.gate, "heldout": nho,
                  "heldout_max_rel_l2": ho_max, "heldout_share": sur.routed, "trusted": sur.trusted},
         "train": {"samples": ntr, "iters": args.learned_iters, "batch": 32, "seconds": t_train,

@@ -5,7 +5,7 @@ a 2-D box to the pressure a fixed number of leapfrog steps later, trained on
 data the PSTD solver produces.  Its spectral layers work in the truncated T1
 basis of each axis (Table 2: C1 for a Neumann pair, S1 for a Dirichlet pair,
 C3 / S3 for mixed walls), which already satisfies the walls, and the solver
-stays the judge: ``Surrogate`` answers with the network only while a held-out
+stays the arbiter: ``Surrogate`` answers with the network only while a held-out
 set and sampled per-request audits stay within a relative error tolerance, and
 runs PSTD otherwise.
 
@@ -400,7 +400,7 @@ def pstd_reference(ncells, bc, dx, cfl, steps, p0s, c0=1500.0, rho0=1000.0, grou
 
 
 class Surrogate:
-    """The learned operator with the solver as judge.
+    """The learned operator with the solver as arbiter.
 
     ``validate`` compares the network with PSTD on a held-out set.  A K-mode
     spectral network cannot carry the part of an input above its K-th mode, so

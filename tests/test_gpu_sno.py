@@ -1,6 +1,6 @@
 """GPU parity of the learned spectral operator: its kernels against numpy, the
 whole network's forward and backward against the FP64 oracle, training, and
-the solver-judged fallback."""
+the fallback to the solver."""
 import ctypes
 
 import numpy as np
@@ -360,7 +360,7 @@ def test_training_reduces_loss_and_fallback():
 def test_learned_operator_on_configured_inputs():
     """The configured workload: 128^2 NN / DD box, 200 steps, inputs of 1-6
     blobs with sigma U[2, 8] dx; trained on 20k PSTD answers (seed 1), gated on
-    512 held-out samples (seed 3), judged on the 1k test set (seed 2).
+    512 held-out samples (seed 3), scored on the 1k test set (seed 2).
 
     A 16-mode network cannot carry an input's content above the 16th mode, so
     on this distribution it is within 1e-2 of PSTD only for its smooth end.
