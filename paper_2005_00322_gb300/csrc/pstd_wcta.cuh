@@ -82,20 +82,6 @@ PSTD_HD void async_wait_all() {
     asm volatile("cp.async.wait_all;\n" ::: "memory");
 #endif
 }
-// Close this thread's group of copies issued so far.
-PSTD_HD void async_commit() {
-#ifdef __CUDA_ARCH__
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-#endif
-}
-// Wait until at most `Pending` of this thread's committed groups are still
-// in flight; a CTA barrier must follow before others read.
-template <int Pending>
-PSTD_HD void async_wait_groups() {
-#ifdef __CUDA_ARCH__
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(Pending) : "memory");
-#endif
-}
 
 struct WAxis {
     int N, L, lp, lo, group2;
@@ -738,21 +724,15 @@ PSTD_HD void step_strided(const WStep& a, int64_t block, float2* smem0, int tid,
     float* rawU = rawP + (size_t)A.G * row_stride(lp, A.G);
     float* rawA = sep ? rawU + (size_t)A.G * row_stride(N, A.G) : rawP;
     pdl_wait();
-    // two groups of copies: the tables and the p tile first, then u_a and the
-    // accumulator, which land while the forward FFT of p runs
     tile_load(a.p, lp, A, o, i0, Gv, rawP, tid, nthr);
-    async_commit();
     tile_load(a.u, N, A, o, i0, Gv, rawU, tid, nthr);
     if (sep) tile_load(a.acc_in, lp, A, o, i0, Gv, rawA, tid, nthr);
-    async_commit();
     // an odd tile's last line pairs with the phantom row Gv (< G)
     const bool phrow = A.ph && (Gv & 1);
     if (phrow)
         for (int m = tid; m < N; m += nthr) rawU[Gv * row_stride(N, A.G) + m] = A.ph[o * N + m];
-    async_wait_groups<1>();
+    async_wait_all();
     PSTD_SYNCCTA();
-    // (every thread of the CTA is a lane of one of its sequences: threads =
-    // seqs x T, so the barriers below are reached by all)
     if (sq < A.seqs) {
         const int ga = 2 * sq, gb = 2 * sq + 1;
         const bool va = ga < Gv, vb = gb < Gv;
@@ -765,9 +745,6 @@ PSTD_HD void step_strided(const WStep& a, int64_t block, float2* smem0, int tid,
         float2 v[E];
         load_p_ext<S>(v, t, A, tab, [&](int i) { return make_float2(va ? pa[i] : 0.0f, vb ? pb[i] : 0.0f); });
         fft<S, false>(v, t, sm, tab);
-        // u_a and the accumulator: every thread's copies have landed
-        async_wait_groups<0>();
-        PSTD_SYNCCTA();
         // the spectrum slots are read from the tile only now, so that they do
         // not occupy registers during the forward FFT
         float2 w[E];
