@@ -129,12 +129,15 @@ int pstd_plan(const pstd_desc* desc, void* stream, pstd_plan_t** out);
  * lengths 256, 512, 768, 1024), variant 2 (length 1024) uses 64 lanes of 16
  * elements, variant 3 (lengths 512, 1024) 128 / 256 lanes of 4 elements (the
  * default for those lengths on axes with too few lines to fill the GPU),
- * variant 4 (lengths 256, 512) variant 1's FFT with its coefficient and
- * twiddle tables read from shared memory instead of registers (fewer
- * registers per thread, more resident CTAs), variant 5 (lengths 256, 512)
- * the same with the tables read from global memory through L1 (neither
- * registers nor shared memory hold them); variants 3, 4 and 5 serve walled
- * (non-periodic) axes only.  An unavailable variant gives PSTD_EINVAL.
+ * variant 4 (lengths 256, 512, 768) variant 1's FFT with its coefficient
+ * and twiddle tables read from shared memory instead of registers (fewer
+ * registers per thread, more resident CTAs; the default for length 768 on
+ * axes with many lines), variant 5 (lengths 256, 512) the same with the
+ * tables read from global memory through L1 (neither registers nor shared
+ * memory hold them; the default for lengths 256 and 512 on axes with many
+ * lines, the 3-D sizes); variants 3, 4 and 5 serve walled (non-periodic)
+ * axes only and fix N = L / 2 at compile time.  An unavailable variant gives
+ * PSTD_EINVAL.
  * seqs_per_cta: line pairs per CTA (a power of two). */
 typedef struct {
     int variant[3];
